@@ -1,0 +1,167 @@
+/*
+ * tm.h -- C ABI of the GB300 (sm_103a) even-odd twisted-mass clover solver library.
+ *
+ * Paper: "Twisted mass ensemble generation on GPU machines" (arXiv 2212.06635).
+ * The library applies the asymmetric even-odd preconditioned operators of Sec. 2
+ * (eq:hQpm for the light doublet, eq:hQh for the non-degenerate heavy doublet)
+ * and solves with them by CG, mixed-precision CG with reliable updates (Sec. 4.1,
+ * "MP-CG") and multishift CG with shift-by-shift refinement (Sec. 4.2).
+ *
+ * Conventions (fixed here; the paper leaves them open):
+ *   dims          {X, Y, Z, T}, each even and >= 2; lex = ((t*Z+z)*Y+y)*X+x;
+ *                 parity = (x+y+z+t) mod 2.  Solves live on ODD sites
+ *                 (ODD_ODD_ASYMMETRIC, Sec. 2); odd site k has lex/2 == k.
+ *   operator      hopping normalisation
+ *                   M = A + i 2 kappa mu g5 - kappa H,
+ *                   H psi(x) = sum_mu (1-g_mu) U_mu(x) psi(x+mu) + (1+g_mu) U_mu(x-mu)^+ psi(x-mu)
+ *                   A = 1 - kappa csw sum_{mu<nu} g_mu g_nu F_munu (clover leaf, traceless),
+ *                 chiral gamma basis with g5 = diag(1,1,-1,-1).  Heavy doublet:
+ *                   M_h = M(mu=0) x 1_f + i 2 kappa mubar g5 tau3 - 2 kappa epsbar tau1.
+ *                 kappa, csw, mu, mubar, epsbar are the bare (mass-normalised) values.
+ *   boundary      periodic in space; bc_t (+1 or -1) multiplies hops across t = T-1 <-> 0.
+ *   canonical     host/device FP64, C order, interleaved complex (re, im):
+ *     gauge       [t][z][y][x][mu 4][row 3][col 3]        mu = 0:x 1:y 2:z 3:t
+ *     odd field   [site_o][spin 4][colour 3]              (light, 24 doubles per site)
+ *                 [site_o][flavour 2][spin 4][colour 3]   (heavy, 48 doubles per site)
+ *   native        the library's own device layout of a field in a storage precision
+ *                 (structure of arrays over sites; 16-bit fields carry one FP32 scale
+ *                 per site).  Obtain sizes with tm_field_bytes and convert with
+ *                 tm_field_import / tm_field_export.
+ *
+ * Ownership: every pointer argument stays owned by the caller; the library copies
+ * what it keeps (gauge field, clover terms) into memory owned by the tm_ctx.
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Operator and field calls are stream-ordered and do not synchronise;
+ * tm_solve_* and tm_power_iteration synchronise `stream` before returning so that
+ * the info records are filled.
+ * Errors: every call returns a tm_status; tm_last_error() returns a message for
+ * the calling thread's most recent failure.  No call aborts the process, and no
+ * kernel traps: device-side failures are reported through status words.
+ */
+#ifndef TM_H
+#define TM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tm_ctx tm_ctx;
+
+typedef enum {
+    TM_OK = 0,
+    TM_ERR_ARG = 1,            /* invalid argument (null pointer, bad size, misaligned) */
+    TM_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+    TM_ERR_OOM = 3,            /* device allocation failed */
+    TM_ERR_STALE = 4,          /* clover term older than the gauge field (call tm_clover_compute) */
+    TM_ERR_NOT_CONVERGED = 5,  /* maxiter reached before the tolerance */
+    TM_ERR_BREAKDOWN = 6,      /* <p, A p> <= 0 or not finite */
+    TM_ERR_TIMEOUT = 7,
+    TM_ERR_UNSUPPORTED = 8
+} tm_status;
+
+typedef enum { TM_F64 = 0, TM_F32 = 1, TM_BF16 = 2, TM_F16 = 3 } tm_prec;
+
+typedef enum {
+    TM_QHAT_PLUS = 0,    /* Q_hat_+  (eq:hQpm, + sign)                          light */
+    TM_QHAT_MINUS = 1,   /* Q_hat_-  = Q_hat_+^dagger                           light */
+    TM_MDAGM = 2,        /* M_hat^dagger M_hat = Q_hat_- Q_hat_+  (HPD)         light */
+    TM_QPQM = 3,         /* Q_hat_+ Q_hat_-  (HMC ordering, HPD)               light */
+    TM_QH = 4,           /* Q_hat_h  (eq:hQh)                                   heavy */
+    TM_QH_DAG = 5,       /* Q_hat_h^dagger = tau1 Q_hat_h tau1 (mubar -> -mubar) heavy */
+    TM_QH_SQ = 6         /* Q_hat_h Q_hat_h^dagger  (HPD)                       heavy */
+} tm_op;
+
+typedef struct {
+    double kappa, csw;
+    double mu;          /* light twisted mass (eq:hQpm) */
+    double mubar;       /* heavy doublet mu_sigma (eq:hQh) */
+    double epsbar;      /* heavy doublet mu_delta (eq:hQh) */
+    int bc_t;           /* +1 periodic, -1 antiperiodic in time */
+} tm_params;
+
+typedef struct {
+    double tol;          /* target FP64 true relative residual ||b - A x|| / ||b|| */
+    int maxiter;         /* bound on Krylov iterations (all restarts together) */
+    tm_prec sloppy;      /* storage precision of the inner iteration; TM_F64 = plain FP64 CG */
+    double delta;        /* reliable-update trigger: ||r_sloppy|| < delta * ||r_true_last|| */
+    int chunk;           /* iterations enqueued between two host checks (0 = default 16) */
+    int use_graph;       /* capture the chunk in a CUDA graph and replay it */
+} tm_solve_params;
+
+typedef struct {
+    int iters;            /* Krylov iterations */
+    int reliable_updates; /* FP64 true-residual recomputations */
+    int status;           /* tm_status of this solve */
+    double true_rel_res;  /* FP64 ||b - A x|| / ||b|| of the returned x */
+    double seconds;       /* wall time of the call */
+} tm_solve_info;
+
+/* Context: one lattice on one device.  dims as above; device = CUDA ordinal.
+ * Fails with TM_ERR_ARG for odd or < 2 extents. */
+tm_status tm_create(tm_ctx** ctx, const int dims[4], int device);
+tm_status tm_destroy(tm_ctx* ctx);
+
+/* Copy a canonical FP64 gauge field (host or device pointer, detected) into the
+ * context and record gauge_id (the position along a trajectory, Sec. 3,
+ * tm_GaugeState_t).  Marks every derived object (low-precision links, clover
+ * terms) stale, as Sec. 3's update_tm_gauge_id cascade does. */
+tm_status tm_gauge_load(tm_ctx* ctx, const double* links, double gauge_id, void* stream);
+tm_status tm_gauge_id(const tm_ctx* ctx, double* gauge_id);
+
+/* Build the clover term A (odd sites) and the even-site inverses
+ * (A_ee +- i 2 kappa mu g5)^-1 and, when mubar or epsbar is non-zero, the heavy
+ * block inverse of eq:hQh, in FP64, and store them in every storage precision
+ * that is later requested.  A no-op when gauge_id and params are unchanged. */
+tm_status tm_clover_compute(tm_ctx* ctx, const tm_params* params, void* stream);
+
+/* Debug/test export of the FP64 clover blocks of all sites of one parity,
+ * layout [site_cb][chirality 2][6][6] complex (chirality 0 = spins 0,1). */
+tm_status tm_clover_export(tm_ctx* ctx, int parity, double* out, void* stream);
+
+/* Bytes of one native odd-site field: nflavour 1 (light) or 2 (heavy). */
+tm_status tm_field_bytes(const tm_ctx* ctx, tm_prec prec, int nflavour, size_t* bytes);
+/* canonical FP64 (device) <-> native (device).  Both pointers 16-byte aligned. */
+tm_status tm_field_import(tm_ctx* ctx, tm_prec prec, int nflavour, void* dst_native,
+                          const double* src_canonical, void* stream);
+tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_canonical,
+                          const void* src_native, void* stream);
+
+/* out = op(in), native fields of precision prec on the device (eq:hQpm / eq:hQh).
+ * Light ops take nflavour-1 fields, heavy ops nflavour-2 fields.  out != in.
+ * Returns TM_ERR_STALE if the clover term predates the gauge field. */
+tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,
+                        void* stream);
+
+/* Solve A x = b, A = TM_MDAGM, TM_QPQM or TM_QH_SQ, by CG (sloppy = TM_F64) or by
+ * mixed-precision CG with reliable updates (Sec. 4.1).  x, b canonical FP64, host
+ * or device pointers; x is the initial guess on entry (zero it for none). */
+tm_status tm_solve_cg(tm_ctx* ctx, tm_op op, const tm_solve_params* sp, double* x,
+                      const double* b, tm_solve_info* info, void* stream);
+
+/* Solve (A + shifts[k]) x[k] = b for nshift shifts (A = TM_MDAGM or TM_QH_SQ) with
+ * one multishift CG in the sloppy precision (Sec. 4.2), then refine each shift
+ * by mixed-precision CG to sp->tol ("shift-by-shift refinement").  x[k] canonical
+ * FP64 output buffers (host or device); infos has nshift records. */
+tm_status tm_solve_multishift(tm_ctx* ctx, tm_op op, int nshift, const double* shifts,
+                              double** x, const double* b, const tm_solve_params* sp,
+                              tm_solve_info* infos, void* stream);
+
+/* n independent solves A_i x_i = b_i on contexts of possibly different volumes, all
+ * advanced together by batched kernels (one launch per step covers every
+ * problem).  n <= 32. */
+tm_status tm_solve_batch(tm_ctx** ctxs, int n, tm_op op, const tm_solve_params* sp,
+                         double** x, const double** b, tm_solve_info* infos, void* stream);
+
+/* Largest eigenvalue of the HPD op (TM_MDAGM, TM_QPQM, TM_QH_SQ) by `iters` power
+ * iterations from a fixed seeded start vector, FP64. */
+tm_status tm_power_iteration(tm_ctx* ctx, tm_op op, int iters, double* lambda_max, void* stream);
+
+/* Message of the calling thread's last failure ("" if none). */
+const char* tm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TM_H */

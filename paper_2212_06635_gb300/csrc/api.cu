@@ -1,0 +1,1138 @@
+// C ABI of include/tm.h: context and gauge-state tracking (Sec. 3), operator
+// application (eq:hQpm, eq:hQh), CG and mixed-precision CG with reliable
+// updates (Sec. 4.1), multishift CG with shift-by-shift refinement (Sec. 4.2),
+// batched solves and power iteration.  All arithmetic runs in the kernels of
+// dslash.cu, blas.cu and gauge.cu; this file only allocates, orders launches and
+// reads back solver control words.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <numeric>
+#include <vector>
+
+#include "tm_host.h"
+
+using namespace tmk;
+
+namespace tmk {
+cudaError_t launch_gauge_import(void* d0, void* d1, const double* src, const Geom& g, cudaStream_t st);
+cudaError_t launch_clover(const Geom& g, const void* g0, const void* g1, int par, double kappa, double csw,
+                          double mu_t, double mubar_t, double epsbar_t, double* outA, double* outB,
+                          double* outH, cudaStream_t st);
+cudaError_t launch_clover_unpack(double* out, const double* A, long vh, cudaStream_t st);
+}  // namespace tmk
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+
+static tm_status fail(tm_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+
+#define CK(...)                                                                               \
+    do {                                                                                      \
+        cudaError_t e_ = (__VA_ARGS__);                                                              \
+        if (e_ != cudaSuccess)                                                                \
+            return fail(e_ == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA, "%s: %s (%s:%d)", \
+                        #__VA_ARGS__, cudaGetErrorString(e_), __FILE__, __LINE__);                   \
+    } while (0)
+#define CKS(...)                             \
+    do {                                     \
+        tm_status s_ = (__VA_ARGS__);               \
+        if (s_ != TM_OK) return s_;          \
+    } while (0)
+
+extern "C" const char* tm_last_error(void) { return g_err; }
+
+// ---------------------------------------------------------------------------
+// small helpers
+// ---------------------------------------------------------------------------
+static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+static inline int nblk(long vh, int bs) { return (int)((vh + bs - 1) / bs); }
+static inline int nflav(tm_op op) { return op >= TM_QH ? 2 : 1; }
+
+static bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static tm_status ws_get(tm_ctx* c, int id, size_t bytes, void** out) {
+    auto it = c->ws.find(id);
+    if (it != c->ws.end() && it->second.second >= bytes) {
+        *out = it->second.first;
+        return TM_OK;
+    }
+    if (it != c->ws.end()) {
+        cudaFree(it->second.first);
+        c->ws.erase(it);
+    }
+    void* p = nullptr;
+    CK(cudaMalloc(&p, bytes));
+    c->ws[id] = {p, bytes};
+    *out = p;
+    return TM_OK;
+}
+
+enum WsId {
+    WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
+    WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
+    WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID,
+    WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
+};
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_create(tm_ctx** out, const int dims[4], int device) {
+    if (!out || !dims) return fail(TM_ERR_ARG, "tm_create: null argument");
+    for (int k = 0; k < 4; ++k)
+        if (dims[k] < 2 || dims[k] % 2) return fail(TM_ERR_ARG, "tm_create: extent %d = %d must be even and >= 2", k, dims[k]);
+    CK(cudaSetDevice(device));
+    tm_ctx* c = new tm_ctx();
+    c->device = device;
+    c->g.X = dims[0]; c->g.Y = dims[1]; c->g.Z = dims[2]; c->g.T = dims[3];
+    c->vh = (long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
+    c->g.vh = c->vh;
+    c->max_blocks = std::max(nblk(c->vh, DSLASH_BS), nblk(c->vh, BLAS_BS));
+    cudaError_t e = cudaSuccess;
+    e = e ? e : cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking);
+    e = e ? e : cudaMalloc(&c->partial, sizeof(double) * c->max_blocks);
+    e = e ? e : cudaMalloc(&c->counter, sizeof(unsigned int) * 4);
+    e = e ? e : cudaMemset(c->counter, 0, sizeof(unsigned int) * 4);
+    e = e ? e : cudaMalloc(&c->ctl, sizeof(SolverCtl));
+    e = e ? e : cudaMemset(c->ctl, 0, sizeof(SolverCtl));
+    e = e ? e : cudaMalloc(&c->ms, sizeof(MsCtl));
+    e = e ? e : cudaMallocHost(&c->h_ctl, sizeof(SolverCtl));
+    e = e ? e : cudaMallocHost(&c->h_ms, sizeof(MsCtl));
+    e = e ? e : cudaMalloc(&c->d_scal, sizeof(double) * 16);
+    e = e ? e : cudaMallocHost(&c->h_scal, sizeof(double) * 16);
+    if (e != cudaSuccess) {
+        tm_destroy(c);
+        return fail(e == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA, "tm_create: %s", cudaGetErrorString(e));
+    }
+    *out = c;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_destroy(tm_ctx* c) {
+    if (!c) return TM_OK;
+    cudaSetDevice(c->device);
+    if (c->sstream) cudaStreamSynchronize(c->sstream);
+    for (int p = 0; p < 2; ++p) { cudaFree(c->gauge64[p]); cudaFree(c->clovA64[p]); }
+    for (int q = 0; q < 4; ++q) {
+        cudaFree(c->gaugeP[q][0]); cudaFree(c->gaugeP[q][1]);
+        cudaFree(c->clovAP[q]); cudaFree(c->clovBP[q]); cudaFree(c->clovHP[q]);
+    }
+    cudaFree(c->clovB64); cudaFree(c->clovH64);
+    cudaFree(c->partial); cudaFree(c->counter); cudaFree(c->ctl); cudaFree(c->ms); cudaFree(c->d_scal);
+    cudaFreeHost(c->h_ctl); cudaFreeHost(c->h_ms); cudaFreeHost(c->h_scal);
+    for (auto& kv : c->ws) cudaFree(kv.second.first);
+    if (c->sstream) cudaStreamDestroy(c->sstream);
+    delete c;
+    return TM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// gauge field and its derived objects (Sec. 3 state cascade)
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_gauge_load(tm_ctx* c, const double* links, double gauge_id, void* stream) {
+    if (!c || !links) return fail(TM_ERR_ARG, "tm_gauge_load: null argument");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    const size_t canon = (size_t)2 * c->vh * 4 * 18 * sizeof(double);
+    for (int p = 0; p < 2; ++p)
+        if (!c->gauge64[p]) CK(cudaMalloc(&c->gauge64[p], link_bytes_parity(P64, c->vh)));
+    const double* src = links;
+    if (!is_device_ptr(links)) {
+        void* stage = nullptr;
+        CKS(ws_get(c, WS_STAGE_G, canon, &stage));
+        CK(cudaMemcpyAsync(stage, links, canon, cudaMemcpyHostToDevice, st));
+        src = reinterpret_cast<const double*>(stage);
+    }
+    CK(launch_gauge_import(c->gauge64[0], c->gauge64[1], src, c->g, st));
+    if (src != links) {
+        CK(cudaStreamSynchronize(st));
+        auto it = c->ws.find(WS_STAGE_G);
+        cudaFree(it->second.first);
+        c->ws.erase(it);
+    }
+    c->gauge_id = gauge_id;
+    c->gauge_gen += 1;   // every derived object is now stale
+    return TM_OK;
+}
+
+extern "C" tm_status tm_gauge_id(const tm_ctx* c, double* id) {
+    if (!c || !id) return fail(TM_ERR_ARG, "tm_gauge_id: null argument");
+    *id = c->gauge_id;
+    return TM_OK;
+}
+
+static bool same_params(const tm_params& a, const tm_params& b) {
+    return a.kappa == b.kappa && a.csw == b.csw && a.mu == b.mu && a.mubar == b.mubar &&
+           a.epsbar == b.epsbar && a.bc_t == b.bc_t;
+}
+
+extern "C" tm_status tm_clover_compute(tm_ctx* c, const tm_params* prm, void* stream) {
+    if (!c || !prm) return fail(TM_ERR_ARG, "tm_clover_compute: null argument");
+    if (c->gauge_gen == 0) return fail(TM_ERR_STALE, "tm_clover_compute: no gauge field loaded");
+    if (prm->bc_t != 1 && prm->bc_t != -1) return fail(TM_ERR_ARG, "tm_clover_compute: bc_t must be +1 or -1");
+    if (!(prm->kappa > 0.0)) return fail(TM_ERR_ARG, "tm_clover_compute: kappa must be positive");
+    CK(cudaSetDevice(c->device));
+    if (c->clover_gauge_gen == c->gauge_gen && same_params(c->params, *prm)) return TM_OK;
+    const cudaStream_t st = S(stream);
+    const long vh = c->vh;
+    const bool heavy = prm->mubar != 0.0 || prm->epsbar != 0.0;
+    for (int p = 0; p < 2; ++p)
+        if (!c->clovA64[p]) CK(cudaMalloc(&c->clovA64[p], sizeof(double) * CLOV_ODD_REALS * vh));
+    if (!c->clovB64) CK(cudaMalloc(&c->clovB64, sizeof(double) * CLOV_EVEN_LIGHT_REALS * vh));
+    if (heavy && !c->clovH64) CK(cudaMalloc(&c->clovH64, sizeof(double) * CLOV_EVEN_HEAVY_REALS * vh));
+    const double k = prm->kappa;
+    CK(launch_clover(c->g, c->gauge64[0], c->gauge64[1], 0, k, prm->csw, 2 * k * prm->mu, 2 * k * prm->mubar,
+                     2 * k * prm->epsbar, c->clovA64[0], c->clovB64, heavy ? c->clovH64 : nullptr, st));
+    CK(launch_clover(c->g, c->gauge64[0], c->gauge64[1], 1, k, prm->csw, 0.0, 0.0, 0.0, c->clovA64[1], nullptr,
+                     nullptr, st));
+    c->params = *prm;
+    c->have_heavy = heavy;
+    c->clover_gauge_gen = c->gauge_gen;
+    c->clover_stamp += 1;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_clover_export(tm_ctx* c, int parity, double* out, void* stream) {
+    if (!c || !out || (parity != 0 && parity != 1)) return fail(TM_ERR_ARG, "tm_clover_export: bad argument");
+    if (c->clover_gauge_gen != c->gauge_gen) return fail(TM_ERR_STALE, "tm_clover_export: clover term is stale");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    const size_t bytes = sizeof(double) * 2 * 2 * 36 * c->vh;
+    if (is_device_ptr(out)) {
+        CK(launch_clover_unpack(out, c->clovA64[parity], c->vh, st));
+    } else {
+        void* tmp = nullptr;
+        CK(cudaMalloc(&tmp, bytes));
+        CK(launch_clover_unpack(reinterpret_cast<double*>(tmp), c->clovA64[parity], c->vh, st));
+        CK(cudaMemcpyAsync(out, tmp, bytes, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        cudaFree(tmp);
+    }
+    return TM_OK;
+}
+
+// make sure the links and clover terms exist in storage precision P
+static tm_status ensure_prec(tm_ctx* c, int P, cudaStream_t st) {
+    if (c->clover_gauge_gen != c->gauge_gen || c->gauge_gen == 0)
+        return fail(TM_ERR_STALE, "clover term is stale: call tm_clover_compute after tm_gauge_load");
+    if (P == P64) return TM_OK;
+    const long vh = c->vh;
+    if (c->gaugeP_gen[P] != c->gauge_gen) {
+        for (int p = 0; p < 2; ++p) {
+            if (!c->gaugeP[P][p]) CK(cudaMalloc(&c->gaugeP[P][p], link_bytes_parity(P, vh)));
+            cudaError_t e = P == P32 ? launch_links_from64<P32>(c->gaugeP[P][p], c->gauge64[p], vh, st)
+                          : P == PB16 ? launch_links_from64<PB16>(c->gaugeP[P][p], c->gauge64[p], vh, st)
+                                      : launch_links_from64<PF16>(c->gaugeP[P][p], c->gauge64[p], vh, st);
+            CK(e);
+        }
+        c->gaugeP_gen[P] = c->gauge_gen;
+    }
+    if (c->clovP_stamp[P] != c->clover_stamp) {
+        const size_t esz = prec_esz(P);
+        auto conv = [&](void** dst, const double* src, int nreal) -> tm_status {
+            if (!*dst) CK(cudaMalloc(dst, esz * nreal * vh));
+            cudaError_t e = P == P32 ? launch_clover_from64<P32>(*dst, src, vh, nreal, st)
+                          : P == PB16 ? launch_clover_from64<PB16>(*dst, src, vh, nreal, st)
+                                      : launch_clover_from64<PF16>(*dst, src, vh, nreal, st);
+            CK(e);
+            return TM_OK;
+        };
+        CKS(conv(&c->clovAP[P], c->clovA64[1], CLOV_ODD_REALS));
+        CKS(conv(&c->clovBP[P], c->clovB64, CLOV_EVEN_LIGHT_REALS));
+        if (c->have_heavy) CKS(conv(&c->clovHP[P], c->clovH64, CLOV_EVEN_HEAVY_REALS));
+        c->clovP_stamp[P] = c->clover_stamp;
+    }
+    return TM_OK;
+}
+
+static const void* gauge_ptr(const tm_ctx* c, int P, int par) { return P == P64 ? c->gauge64[par] : c->gaugeP[P][par]; }
+static const void* clovA_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovA64[1] : c->clovAP[P]; }
+static const void* clovB_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovB64 : c->clovBP[P]; }
+static const void* clovH_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovH64 : c->clovHP[P]; }
+
+// ---------------------------------------------------------------------------
+// operator application
+// ---------------------------------------------------------------------------
+static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void* out, const void* in,
+                        const void* loc, SolverCtl* ctl, bool fuse) {
+    OpProb p{};
+    p.g = c->g;
+    p.nblk = nblk(c->vh, DSLASH_BS);
+    p.bc_t = (float)c->params.bc_t;
+    p.gauge[0] = gauge_ptr(c, P, 0);
+    p.gauge[1] = gauge_ptr(c, P, 1);
+    p.clov = kind == K1_EO_INV ? (nf == 1 ? clovB_ptr(c, P) : clovH_ptr(c, P)) : clovA_ptr(c, P);
+    p.in = in;
+    p.loc = loc;
+    p.out = out;
+    const double k = c->params.kappa;
+    p.kappa = k;
+    p.tw = sign * 2.0 * k * (nf == 1 ? c->params.mu : c->params.mubar);
+    p.eps = 2.0 * k * c->params.epsbar;
+    p.sign = sign;
+    p.ctl = ctl;
+    p.ms = c->ms;
+    p.partial = fuse ? c->partial : nullptr;
+    p.counter = c->counter;
+    return p;
+}
+
+// out = Q_hat(sign) in, via the even temporary te.  fin != FIN_NONE fuses ||out||^2.
+template <int P, int NF>
+static cudaError_t schur(const tm_ctx* c, int sign, void* out, const void* in, void* te, cudaStream_t st,
+                         SolverCtl* ctl, int fin) {
+    OpBatch<1> b{};
+    b.n = 1;
+    b.fin = FIN_NONE;
+    const int nb = nblk(c->vh, DSLASH_BS);
+    b.blk_start[0] = 0;
+    b.blk_start[1] = nb;
+    b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, ctl, false);
+    cudaError_t e = launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st);
+    if (e != cudaSuccess) return e;
+    b.fin = fin;
+    b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, ctl, fin != FIN_NONE);
+    return launch_dslash<P, NF, K2_OE_LOCAL, 1>(b, nb, st);
+}
+
+// signs of the two factors of a normal operator (first applied first)
+static void normal_signs(tm_op op, int* s1, int* s2) {
+    if (op == TM_MDAGM) { *s1 = +1; *s2 = -1; }        // Q- Q+
+    else if (op == TM_QPQM) { *s1 = -1; *s2 = +1; }    // Q+ Q-
+    else { *s1 = -1; *s2 = +1; }                       // Qh Qh^+
+}
+
+// out = A in for a normal op, fin fused into the first factor (||Q in||^2 = <in, A in>)
+template <int P, int NF>
+static cudaError_t normal_op(const tm_ctx* c, tm_op op, void* out, const void* in, void* mid, void* te,
+                             cudaStream_t st, SolverCtl* ctl, int fin) {
+    int s1, s2;
+    normal_signs(op, &s1, &s2);
+    cudaError_t e = schur<P, NF>(c, s1, mid, in, te, st, ctl, fin);
+    if (e != cudaSuccess) return e;
+    return schur<P, NF>(c, s2, out, mid, te, st, ctl, FIN_NONE);
+}
+
+template <int P, int NF>
+static tm_status apply_t(tm_ctx* c, tm_op op, void* out, const void* in, cudaStream_t st) {
+    void *te = nullptr, *mid = nullptr;
+    CKS(ws_get(c, WS_APPLY_TE, spinor_bytes(P, 12 * NF, c->vh), &te));
+    if (op == TM_QHAT_PLUS || op == TM_QH) {
+        CK(schur<P, NF>(c, +1, out, in, te, st, nullptr, FIN_NONE));
+    } else if (op == TM_QHAT_MINUS || op == TM_QH_DAG) {
+        CK(schur<P, NF>(c, -1, out, in, te, st, nullptr, FIN_NONE));
+    } else {
+        CKS(ws_get(c, WS_APPLY_MID, spinor_bytes(P, 12 * NF, c->vh), &mid));
+        CK(normal_op<P, NF>(c, op, out, in, mid, te, st, nullptr, FIN_NONE));
+    }
+    return TM_OK;
+}
+
+static tm_status check_prec(int p) {
+    if (p < TM_F64 || p > TM_F16) return fail(TM_ERR_ARG, "unknown precision %d", p);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_apply_Mhat(tm_ctx* c, tm_op op, tm_prec prec, void* out, const void* in, void* stream) {
+    if (!c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_apply_Mhat: bad pointers");
+    if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_Mhat: fields must be 16-byte aligned");
+    if (op < TM_QHAT_PLUS || op > TM_QH_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown op %d", (int)op);
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ensure_prec(c, prec, st));
+    if (nflav(op) == 2 && !c->have_heavy)
+        return fail(TM_ERR_ARG, "tm_apply_Mhat: heavy operator needs mubar or epsbar in tm_clover_compute");
+    const bool h = nflav(op) == 2;
+    switch (prec) {
+        case TM_F64: return h ? apply_t<P64, 2>(c, op, out, in, st) : apply_t<P64, 1>(c, op, out, in, st);
+        case TM_F32: return h ? apply_t<P32, 2>(c, op, out, in, st) : apply_t<P32, 1>(c, op, out, in, st);
+        case TM_BF16: return h ? apply_t<PB16, 2>(c, op, out, in, st) : apply_t<PB16, 1>(c, op, out, in, st);
+        case TM_F16: return h ? apply_t<PF16, 2>(c, op, out, in, st) : apply_t<PF16, 1>(c, op, out, in, st);
+    }
+    return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown precision");
+}
+
+// ---------------------------------------------------------------------------
+// fields
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_field_bytes(const tm_ctx* c, tm_prec prec, int nf, size_t* bytes) {
+    if (!c || !bytes || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_bytes: bad argument");
+    CKS(check_prec(prec));
+    *bytes = spinor_bytes(prec, 12 * nf, c->vh);
+    return TM_OK;
+}
+
+template <int P>
+static cudaError_t import_t(int nf, void* d, const double* s, long vh, cudaStream_t st) {
+    return nf == 1 ? launch_import<P, 12>(d, s, vh, st) : launch_import<P, 24>(d, s, vh, st);
+}
+template <int P>
+static cudaError_t export_t(int nf, double* d, const void* s, long vh, cudaStream_t st) {
+    return nf == 1 ? launch_export<P, 12>(d, s, vh, st) : launch_export<P, 24>(d, s, vh, st);
+}
+
+static cudaError_t import_any(int prec, int nf, void* d, const double* s, long vh, cudaStream_t st) {
+    switch (prec) {
+        case P64: return import_t<P64>(nf, d, s, vh, st);
+        case P32: return import_t<P32>(nf, d, s, vh, st);
+        case PB16: return import_t<PB16>(nf, d, s, vh, st);
+        default: return import_t<PF16>(nf, d, s, vh, st);
+    }
+}
+static cudaError_t export_any(int prec, int nf, double* d, const void* s, long vh, cudaStream_t st) {
+    switch (prec) {
+        case P64: return export_t<P64>(nf, d, s, vh, st);
+        case P32: return export_t<P32>(nf, d, s, vh, st);
+        case PB16: return export_t<PB16>(nf, d, s, vh, st);
+        default: return export_t<PF16>(nf, d, s, vh, st);
+    }
+}
+
+extern "C" tm_status tm_field_import(tm_ctx* c, tm_prec prec, int nf, void* dst, const double* src, void* stream) {
+    if (!c || !dst || !src || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_import: bad argument");
+    if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_import: pointers must be 16-byte aligned");
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    CK(import_any(prec, nf, dst, src, c->vh, S(stream)));
+    return TM_OK;
+}
+
+extern "C" tm_status tm_field_export(tm_ctx* c, tm_prec prec, int nf, double* dst, const void* src, void* stream) {
+    if (!c || !dst || !src || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_export: bad argument");
+    if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_export: pointers must be 16-byte aligned");
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    CK(export_any(prec, nf, dst, src, c->vh, S(stream)));
+    return TM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solver building blocks (single problem)
+// ---------------------------------------------------------------------------
+static VecBatch<1> vb1(const tm_ctx* c, void* v0, void* v1 = nullptr, void* v2 = nullptr, void* v3 = nullptr,
+                       double* dst = nullptr) {
+    VecBatch<1> b{};
+    b.n = 1;
+    const int nb = nblk(c->vh, BLAS_BS);
+    b.blk_start[0] = 0;
+    b.blk_start[1] = nb;
+    VecProb& p = b.p[0];
+    p.vh = c->vh;
+    p.nblk = nb;
+    p.v[0] = v0; p.v[1] = v1; p.v[2] = v2; p.v[3] = v3;
+    p.ctl = c->ctl;
+    p.ms = c->ms;
+    p.partial = c->partial;
+    p.counter = c->counter;
+    p.dst = dst;
+    return b;
+}
+
+static tm_status read_scalar(tm_ctx* c, double* dev, double* out, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_scal, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *out = c->h_scal[0];
+    return TM_OK;
+}
+
+static tm_status put_ctl(tm_ctx* c, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->ctl, c->h_ctl, sizeof(SolverCtl), cudaMemcpyHostToDevice, st));
+    return TM_OK;
+}
+static tm_status get_ctl(tm_ctx* c, cudaStream_t st) {
+    CK(cudaMemcpyAsync(c->h_ctl, c->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return TM_OK;
+}
+
+// r64 = b64 - (A + shift) x64, returns ||r64||^2
+template <int NF>
+static tm_status true_residual(tm_ctx* c, tm_op op, double shift, void* x64, void* b64, void* r64, void* ax64,
+                               void* mid64, void* te64, cudaStream_t st, double* rr) {
+    CK((normal_op<P64, NF>(c, op, ax64, x64, mid64, te64, st, nullptr, FIN_NONE)));
+    c->h_ctl->shift = shift;
+    CK(cudaMemcpyAsync(&c->ctl->shift, &c->h_ctl->shift, sizeof(double), cudaMemcpyHostToDevice, st));
+    CK((launch_residual64<12 * NF, 1>(vb1(c, r64, b64, ax64, x64, c->d_scal), nblk(c->vh, BLAS_BS), st)));
+    return read_scalar(c, c->d_scal, rr, st);
+}
+
+template <int P, int NC>
+static tm_status norm2_dev(tm_ctx* c, const void* v, cudaStream_t st, double* out) {
+    CK((launch_norm2<P, NC, 1>(vb1(c, const_cast<void*>(v), nullptr, nullptr, nullptr, c->d_scal),
+                                nblk(c->vh, BLAS_BS), st)));
+    return read_scalar(c, c->d_scal, out, st);
+}
+
+// One CG iteration in storage precision PS (x accumulated in PX):
+//   p = r + beta p;  Ap (fused <p,Ap> -> alpha);  x += alpha p, r -= alpha Ap (fused rr -> beta, flag)
+template <int PS, int NF>
+static cudaError_t cg_iteration(tm_ctx* c, tm_op op, void* xs, void* p, void* r, void* ap, void* mid, void* te,
+                                cudaStream_t st) {
+    constexpr int PX = PS == P64 ? P64 : P32;
+    const int nb = nblk(c->vh, BLAS_BS);
+    cudaError_t e = launch_cg_pupdate<PS, 12 * NF, 1>(vb1(c, p, r), nb, st);
+    if (e != cudaSuccess) return e;
+    e = normal_op<PS, NF>(c, op, ap, p, mid, te, st, c->ctl, FIN_CG_ALPHA);
+    if (e != cudaSuccess) return e;
+    return launch_cg_update<PS, PX, 12 * NF, 1>(vb1(c, xs, p, r, ap), nb, st);
+}
+
+// Solve (A + shift) x = b in place on native FP64 x64, b64.
+// PS == P64: plain FP64 CG.  Otherwise mixed precision with reliable updates:
+// the iteration runs in PS storage / FP32 arithmetic with x accumulated in FP32;
+// whenever ||r|| has dropped by delta since the last true residual, x is folded
+// into the FP64 solution and r is recomputed as b - A x in FP64.
+template <int PS, int NF>
+static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_params* sp, void* x64, void* b64,
+                            tm_solve_info* info, cudaStream_t st) {
+    constexpr int NC = 12 * NF;
+    const long vh = c->vh;
+    const size_t b64sz = spinor_bytes(P64, NC, vh), bssz = spinor_bytes(PS, NC, vh);
+    void *r64, *ax64, *te64, *mid64;
+    CKS(ws_get(c, WS_R64, b64sz, &r64));
+    CKS(ws_get(c, WS_AX64, b64sz, &ax64));
+    CKS(ws_get(c, WS_TE64, b64sz, &te64));
+    CKS(ws_get(c, WS_MID64, b64sz, &mid64));
+    void *rs, *ps, *aps, *tes, *mids, *xs;
+    if (PS == P64) {
+        rs = r64; xs = x64; tes = te64; mids = mid64;
+        CKS(ws_get(c, WS_P_S, bssz, &ps));
+        CKS(ws_get(c, WS_AP_S, bssz, &aps));
+    } else {
+        CKS(ws_get(c, WS_R_S, bssz, &rs));
+        CKS(ws_get(c, WS_P_S, bssz, &ps));
+        CKS(ws_get(c, WS_AP_S, bssz, &aps));
+        CKS(ws_get(c, WS_TE_S, bssz, &tes));
+        CKS(ws_get(c, WS_MID_S, bssz, &mids));
+        CKS(ws_get(c, WS_X_S, spinor_bytes(P32, NC, vh), &xs));
+    }
+    const double tol = sp->tol > 0 ? sp->tol : 1e-10;
+    const int maxiter = sp->maxiter > 0 ? sp->maxiter : 100000;
+    const double delta = PS == P64 ? 0.0 : (sp->delta > 0 ? sp->delta : 0.1);
+    const int chunk = sp->chunk > 0 ? sp->chunk : 16;
+    const int nb = nblk(vh, BLAS_BS);
+
+    double bb = 0;
+    CKS((norm2_dev<P64, NC>(c, b64, st, &bb)));
+    info->iters = 0;
+    info->reliable_updates = 0;
+    if (!(bb > 0)) {
+        CK(cudaMemsetAsync(x64, 0, b64sz, st));
+        info->true_rel_res = 0.0;
+        info->status = TM_OK;
+        return TM_OK;
+    }
+    double rr = 0;
+    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
+    const double target = tol * tol * bb;
+    tm_status status = TM_OK;
+    cudaGraphExec_t gexec = nullptr;
+    if (rr > target) {
+        if (PS != P64) {
+            CK((launch_convert<PS, P64, NC, 1>(vb1(c, rs, r64), nb, st)));
+            CK(cudaMemsetAsync(xs, 0, spinor_bytes(P32, NC, vh), st));
+        }
+        SolverCtl& h = *c->h_ctl;
+        std::memset(&h, 0, sizeof(SolverCtl));
+        h.rr = rr;
+        h.rr_old = rr;
+        h.beta = 0.0;
+        h.shift = shift;
+        h.maxiter = maxiter;
+        h.stop_rr = std::max(target, delta * delta * rr);
+        h.flag = CTL_RUN;
+        CKS(put_ctl(c, st));
+        if (sp->use_graph) {
+            cudaGraph_t graph;
+            CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+            for (int it = 0; it < chunk; ++it) {
+                cudaError_t e = cg_iteration<PS, NF>(c, op, xs, ps, rs, aps, mids, tes, st);
+                if (e != cudaSuccess) {
+                    cudaStreamEndCapture(st, &graph);
+                    return fail(TM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+                }
+            }
+            CK(cudaStreamEndCapture(st, &graph));
+            CK(cudaGraphInstantiate(&gexec, graph, 0));
+            cudaGraphDestroy(graph);
+        }
+        for (;;) {
+            if (gexec) {
+                CK(cudaGraphLaunch(gexec, st));
+            } else {
+                for (int it = 0; it < chunk; ++it) CK((cg_iteration<PS, NF>(c, op, xs, ps, rs, aps, mids, tes, st)));
+            }
+            CKS(get_ctl(c, st));
+            if (h.flag == CTL_RUN) continue;
+            if (h.flag == CTL_BREAKDOWN) { status = TM_ERR_BREAKDOWN; break; }
+            // reliable update / convergence check in FP64
+            if (PS != P64) {
+                CK((launch_add_to64<P32, NC, 1>(vb1(c, x64, xs), nb, st)));
+                CK(cudaMemsetAsync(xs, 0, spinor_bytes(P32, NC, vh), st));
+            }
+            CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
+            info->reliable_updates += 1;
+            if (rr <= target) break;
+            if (h.flag == CTL_MAXITER || h.iter >= maxiter || !std::isfinite(rr)) {
+                status = std::isfinite(rr) ? TM_ERR_NOT_CONVERGED : TM_ERR_BREAKDOWN;
+                break;
+            }
+            if (PS != P64) CK((launch_convert<PS, P64, NC, 1>(vb1(c, rs, r64), nb, st)));
+            h.beta = rr / h.rr_old;
+            h.rr = rr;
+            h.stop_rr = std::max(target, delta * delta * rr);
+            h.flag = CTL_RUN;
+            CKS(put_ctl(c, st));
+        }
+        info->iters = h.iter;
+        if (gexec) cudaGraphExecDestroy(gexec);
+    }
+    info->true_rel_res = std::sqrt(rr / bb);
+    info->status = status;
+    if (status != TM_OK)
+        fail(status, "solve: %s after %d iterations, true rel res %.3e",
+             status == TM_ERR_BREAKDOWN ? "breakdown" : "not converged", info->iters, info->true_rel_res);
+    return status;
+}
+
+template <int NF>
+static tm_status solve_dispatch(tm_ctx* c, tm_op op, double shift, const tm_solve_params* sp, void* x64, void* b64,
+                                tm_solve_info* info, cudaStream_t st) {
+    switch (sp->sloppy) {
+        case TM_F64: return solve_core<P64, NF>(c, op, shift, sp, x64, b64, info, st);
+        case TM_F32: return solve_core<P32, NF>(c, op, shift, sp, x64, b64, info, st);
+        case TM_BF16: return solve_core<PB16, NF>(c, op, shift, sp, x64, b64, info, st);
+        case TM_F16: return solve_core<PF16, NF>(c, op, shift, sp, x64, b64, info, st);
+    }
+    return fail(TM_ERR_ARG, "unknown sloppy precision");
+}
+
+// canonical (host or device) <-> native FP64 working copies
+static tm_status stage_in(tm_ctx* c, int nf, const double* canon, int stage_id, void* native64, cudaStream_t st) {
+    const size_t bytes = sizeof(double) * 24 * nf * c->vh;
+    const double* src = canon;
+    if (!is_device_ptr(canon)) {
+        void* s = nullptr;
+        CKS(ws_get(c, stage_id, bytes, &s));
+        CK(cudaMemcpyAsync(s, canon, bytes, cudaMemcpyHostToDevice, st));
+        src = reinterpret_cast<const double*>(s);
+    }
+    CK(import_any(P64, nf, native64, src, c->vh, st));
+    return TM_OK;
+}
+static tm_status stage_out(tm_ctx* c, int nf, double* canon, int stage_id, const void* native64, cudaStream_t st) {
+    const size_t bytes = sizeof(double) * 24 * nf * c->vh;
+    if (is_device_ptr(canon)) {
+        CK(export_any(P64, nf, canon, native64, c->vh, st));
+    } else {
+        void* s = nullptr;
+        CKS(ws_get(c, stage_id, bytes, &s));
+        CK(export_any(P64, nf, reinterpret_cast<double*>(s), native64, c->vh, st));
+        CK(cudaMemcpyAsync(canon, s, bytes, cudaMemcpyDeviceToHost, st));
+    }
+    return TM_OK;
+}
+
+static tm_status enter_solver(tm_ctx* c, void* stream) {
+    // order the private solver stream after the caller's stream
+    cudaEvent_t ev;
+    CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CK(cudaEventRecord(ev, S(stream)));
+    CK(cudaStreamWaitEvent(c->sstream, ev, 0));
+    cudaEventDestroy(ev);
+    return TM_OK;
+}
+
+static tm_status check_solver_op(tm_ctx* c, tm_op op) {
+    if (op != TM_MDAGM && op != TM_QPQM && op != TM_QH_SQ)
+        return fail(TM_ERR_ARG, "solver op must be TM_MDAGM, TM_QPQM or TM_QH_SQ");
+    if (op == TM_QH_SQ && !c->have_heavy)
+        return fail(TM_ERR_ARG, "heavy operator needs mubar or epsbar in tm_clover_compute");
+    return TM_OK;
+}
+
+extern "C" tm_status tm_solve_cg(tm_ctx* c, tm_op op, const tm_solve_params* sp, double* x, const double* b,
+                                 tm_solve_info* info, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !sp || !x || !b || !info) return fail(TM_ERR_ARG, "tm_solve_cg: null argument");
+    CKS(check_prec(sp->sloppy));
+    CK(cudaSetDevice(c->device));
+    CKS(check_solver_op(c, op));
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ensure_prec(c, P64, st));
+    CKS(ensure_prec(c, sp->sloppy, st));
+    const int nf = nflav(op);
+    void *x64, *b64;
+    CKS(ws_get(c, WS_X64, spinor_bytes(P64, 12 * nf, c->vh), &x64));
+    CKS(ws_get(c, WS_B64, spinor_bytes(P64, 12 * nf, c->vh), &b64));
+    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
+    CKS(stage_in(c, nf, x, WS_STAGE_X, x64, st));
+    tm_status s = nf == 1 ? solve_dispatch<1>(c, op, 0.0, sp, x64, b64, info, st)
+                          : solve_dispatch<2>(c, op, 0.0, sp, x64, b64, info, st);
+    CKS(stage_out(c, nf, x, WS_STAGE_X, x64, st));
+    CK(cudaStreamSynchronize(st));
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return s;
+}
+
+// ---------------------------------------------------------------------------
+// multishift CG (Sec. 4.2) with shift-by-shift refinement
+// ---------------------------------------------------------------------------
+template <int PS, int NF>
+static tm_status multishift_core(tm_ctx* c, tm_op op, int ns, const double* sh_sorted, void* b64,
+                                 const tm_solve_params* sp, std::vector<void*>& xk64, int* iters,
+                                 cudaStream_t st) {
+    constexpr int NC = 12 * NF;
+    constexpr int PX = PS == P64 ? P64 : P32;
+    const long vh = c->vh;
+    const size_t bs = spinor_bytes(PS, NC, vh), bx = spinor_bytes(PX, NC, vh);
+    void *rs, *ps, *aps, *tes, *mids;
+    CKS(ws_get(c, WS_R_S, bs, &rs));
+    CKS(ws_get(c, WS_P_S, bs, &ps));
+    CKS(ws_get(c, WS_AP_S, bs, &aps));
+    CKS(ws_get(c, WS_TE_S, bs, &tes));
+    CKS(ws_get(c, WS_MID_S, bs, &mids));
+    MsVecs mv{};
+    for (int k = 0; k < ns; ++k) {
+        CKS(ws_get(c, WS_MS_P + k, bs, &mv.p[k]));
+        if (PX == P64) {
+            mv.x[k] = xk64[k];
+        } else {
+            CKS(ws_get(c, WS_MS_X + k, bx, &mv.x[k]));
+        }
+        CK(cudaMemsetAsync(mv.x[k], 0, bx, st));
+    }
+    const int nb = nblk(vh, BLAS_BS);
+    double bb;
+    CKS((norm2_dev<P64, NC>(c, b64, st, &bb)));
+    CK((launch_convert<PS, P64, NC, 1>(vb1(c, rs, b64), nb, st)));
+    // the sloppy multishift stops each shift near the precision floor of PS
+    const double floor_tol = PS == P64 ? 0.0 : (PS == P32 ? 1e-6 : 2e-4);
+    const double ms_tol = std::max(sp->tol, floor_tol);
+    MsCtl& m = *c->h_ms;
+    std::memset(&m, 0, sizeof(MsCtl));
+    for (int k = 0; k < ns; ++k) {
+        m.zeta[k] = m.zeta_old[k] = 1.0;
+        m.dshift[k] = sh_sorted[k] - sh_sorted[0];
+        m.active[k] = 1;
+    }
+    m.alpha_old = 1.0;
+    m.beta_old = 0.0;
+    m.nshift = ns;
+    m.n_active = ns;
+    m.stop_rr = ms_tol * ms_tol * bb;
+    CK(cudaMemcpyAsync(c->ms, &m, sizeof(MsCtl), cudaMemcpyHostToDevice, st));
+    SolverCtl& h = *c->h_ctl;
+    std::memset(&h, 0, sizeof(SolverCtl));
+    h.rr = bb;
+    h.rr_old = bb;
+    h.shift = sh_sorted[0];
+    h.maxiter = sp->maxiter > 0 ? sp->maxiter : 100000;
+    h.stop_rr = 0.0;
+    h.flag = CTL_RUN;
+    CKS(put_ctl(c, st));
+    auto iteration = [&](int first) -> cudaError_t {
+        cudaError_t e = launch_ms_pupdate<PS, PX, NC>(vb1(c, rs, ps), mv, first, nb, st);
+        if (e != cudaSuccess) return e;
+        e = normal_op<PS, NF>(c, op, aps, ps, mids, tes, st, c->ctl, FIN_MS_ALPHA);
+        if (e != cudaSuccess) return e;
+        return launch_ms_update<PS, NC>(vb1(c, rs, ps, aps), nb, st);
+    };
+    CK(iteration(1));
+    const int chunk = sp->chunk > 0 ? sp->chunk : 16;
+    cudaGraphExec_t gexec = nullptr;
+    if (sp->use_graph) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < chunk; ++it) {
+            cudaError_t e = iteration(0);
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(st, &graph);
+                return fail(TM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+            }
+        }
+        CK(cudaStreamEndCapture(st, &graph));
+        CK(cudaGraphInstantiate(&gexec, graph, 0));
+        cudaGraphDestroy(graph);
+    }
+    tm_status status = TM_OK;
+    for (;;) {
+        CKS(get_ctl(c, st));
+        if (h.flag != CTL_RUN) break;
+        if (gexec) {
+            CK(cudaGraphLaunch(gexec, st));
+        } else {
+            for (int it = 0; it < chunk; ++it) CK(iteration(0));
+        }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    if (h.flag == CTL_BREAKDOWN) status = fail(TM_ERR_BREAKDOWN, "multishift: breakdown");
+    CK((launch_ms_finish<PS, PX, NC>(vb1(c, rs, ps), mv, nb, st)));
+    // hand the sloppy solutions to FP64
+    if (PX != P64) {
+        for (int k = 0; k < ns; ++k) {
+            CK(cudaMemsetAsync(xk64[k], 0, spinor_bytes(P64, NC, vh), st));
+            CK((launch_add_to64<P32, NC, 1>(vb1(c, xk64[k], mv.x[k]), nb, st)));
+        }
+    }
+    *iters = h.iter;
+    return status;
+}
+
+template <int NF>
+static tm_status multishift_dispatch(tm_ctx* c, tm_op op, int ns, const double* sh, void* b64,
+                                     const tm_solve_params* sp, std::vector<void*>& xk64, int* iters,
+                                     cudaStream_t st) {
+    switch (sp->sloppy) {
+        case TM_F64: return multishift_core<P64, NF>(c, op, ns, sh, b64, sp, xk64, iters, st);
+        case TM_F32: return multishift_core<P32, NF>(c, op, ns, sh, b64, sp, xk64, iters, st);
+        case TM_BF16: return multishift_core<PB16, NF>(c, op, ns, sh, b64, sp, xk64, iters, st);
+        case TM_F16: return multishift_core<PF16, NF>(c, op, ns, sh, b64, sp, xk64, iters, st);
+    }
+    return fail(TM_ERR_ARG, "unknown sloppy precision");
+}
+
+extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const double* shifts, double** x,
+                                         const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                                         void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !shifts || !x || !b || !sp || !infos) return fail(TM_ERR_ARG, "tm_solve_multishift: null argument");
+    if (ns < 1 || ns > MAX_SHIFTS) return fail(TM_ERR_ARG, "tm_solve_multishift: 1 <= nshift <= %d", MAX_SHIFTS);
+    for (int k = 0; k < ns; ++k)
+        if (!(shifts[k] >= 0.0) || !x[k]) return fail(TM_ERR_ARG, "tm_solve_multishift: shifts must be >= 0");
+    if (op != TM_MDAGM && op != TM_QH_SQ && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_solve_multishift: bad op");
+    CKS(check_prec(sp->sloppy));
+    CK(cudaSetDevice(c->device));
+    CKS(check_solver_op(c, op));
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ensure_prec(c, P64, st));
+    CKS(ensure_prec(c, sp->sloppy, st));
+    const int nf = nflav(op);
+    const size_t b64sz = spinor_bytes(P64, 12 * nf, c->vh);
+    std::vector<int> order(ns);
+    std::iota(order.begin(), order.end(), 0);
+    std::stable_sort(order.begin(), order.end(), [&](int a, int bq) { return shifts[a] < shifts[bq]; });
+    std::vector<double> sh(ns);
+    for (int k = 0; k < ns; ++k) sh[k] = shifts[order[k]];
+    void* b64;
+    CKS(ws_get(c, WS_B64, b64sz, &b64));
+    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
+    std::vector<void*> xk64(ns);
+    for (int k = 0; k < ns; ++k) CKS(ws_get(c, WS_MS_X64 + k, b64sz, &xk64[k]));
+    int ms_iters = 0;
+    tm_status s = nf == 1 ? multishift_dispatch<1>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st)
+                          : multishift_dispatch<2>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st);
+    tm_status worst = s;
+    // shift-by-shift refinement with mixed-precision CG (Sec. 4.2)
+    for (int k = 0; k < ns; ++k) {
+        tm_solve_info& inf = infos[order[k]];
+        std::memset(&inf, 0, sizeof(inf));
+        if (s != TM_OK) { inf.status = s; continue; }
+        tm_status r = nf == 1 ? solve_dispatch<1>(c, op, sh[k], sp, xk64[k], b64, &inf, st)
+                              : solve_dispatch<2>(c, op, sh[k], sp, xk64[k], b64, &inf, st);
+        inf.iters += ms_iters;
+        if (r != TM_OK && worst == TM_OK) worst = r;
+        CKS(stage_out(c, nf, x[order[k]], WS_STAGE_X, xk64[k], st));
+        CK(cudaStreamSynchronize(st));
+    }
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < ns; ++k) infos[k].seconds = secs;
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// power iteration
+// ---------------------------------------------------------------------------
+template <int NF>
+static tm_status power_core(tm_ctx* c, tm_op op, int iters, double* lam, cudaStream_t st) {
+    constexpr int NC = 12 * NF;
+    const long vh = c->vh;
+    const size_t sz = spinor_bytes(P64, NC, vh);
+    void *v, *w, *te, *mid;
+    CKS(ws_get(c, WS_V64, sz, &v));
+    CKS(ws_get(c, WS_AX64, sz, &w));
+    CKS(ws_get(c, WS_TE64, sz, &te));
+    CKS(ws_get(c, WS_MID64, sz, &mid));
+    // fixed start vector (splitmix64 of the component index), made on the host
+    std::vector<double> h((size_t)2 * NC * vh);
+    uint64_t s = 0x9e3779b97f4a7c15ull;
+    for (size_t k = 0; k < h.size(); ++k) {
+        uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        h[k] = (double)(z >> 11) * (1.0 / 9007199254740992.0) - 0.5;
+    }
+    void* stage;
+    CKS(ws_get(c, WS_STAGE_B, h.size() * sizeof(double), &stage));
+    CK(cudaMemcpyAsync(stage, h.data(), h.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(import_any(P64, NF, v, reinterpret_cast<const double*>(stage), vh, st));
+    CK(cudaStreamSynchronize(st));
+    const int nb = nblk(vh, BLAS_BS);
+    CK((launch_norm2<P64, NC, 1>(vb1(c, v, nullptr, nullptr, nullptr, c->d_scal), nb, st)));
+    CK((launch_normalize64<NC>(vb1(c, v, nullptr, nullptr, nullptr, c->d_scal), nb, st)));
+    std::memset(c->h_ctl, 0, sizeof(SolverCtl));
+    CKS(put_ctl(c, st));
+    for (int it = 0; it < iters; ++it) {
+        // <v, A v> = ||Q v||^2 (fused, FIN_STORE -> ctl->result); w = A v; v = w / ||w||
+        CK((normal_op<P64, NF>(c, op, w, v, mid, te, st, c->ctl, FIN_STORE)));
+        CK((launch_norm2<P64, NC, 1>(vb1(c, w, nullptr, nullptr, nullptr, c->d_scal), nb, st)));
+        CK((launch_normalize64<NC>(vb1(c, w, nullptr, nullptr, nullptr, c->d_scal), nb, st)));
+        std::swap(v, w);
+    }
+    CKS(get_ctl(c, st));
+    *lam = c->h_ctl->result;
+    // keep the workspace map consistent with the swapped buffers
+    c->ws[WS_V64].first = v;
+    c->ws[WS_AX64].first = w;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_power_iteration(tm_ctx* c, tm_op op, int iters, double* lam, void* stream) {
+    if (!c || !lam || iters < 1) return fail(TM_ERR_ARG, "tm_power_iteration: bad argument");
+    CK(cudaSetDevice(c->device));
+    CKS(check_solver_op(c, op));
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ensure_prec(c, P64, st));
+    return nflav(op) == 1 ? power_core<1>(c, op, iters, lam, st) : power_core<2>(c, op, iters, lam, st);
+}
+
+// ---------------------------------------------------------------------------
+// batched solves: every step of every problem in one launch per kernel
+// ---------------------------------------------------------------------------
+struct BatchWs {
+    void *x64, *b64, *rs, *ps, *aps, *tes, *mids, *xs;
+};
+
+template <int PS>
+static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params* sp, std::vector<BatchWs>& w,
+                            tm_solve_info* infos, cudaStream_t st) {
+    constexpr int NC = 12;
+    constexpr int PX = PS == P64 ? P64 : P32;
+    const double tol = sp->tol > 0 ? sp->tol : 1e-10;
+    const int maxiter = sp->maxiter > 0 ? sp->maxiter : 100000;
+    const double delta = PS == P64 ? 0.0 : (sp->delta > 0 ? sp->delta : 0.1);
+    const int chunk = sp->chunk > 0 ? sp->chunk : 16;
+    std::vector<double> bb(n), rr(n);
+    std::vector<int> done(n, 0);
+    // per-problem set-up: true residual, sloppy copies, control words
+    for (int q = 0; q < n; ++q) {
+        tm_ctx* c = cs[q];
+        void *r64, *ax64, *te64, *mid64;
+        const size_t sz = spinor_bytes(P64, NC, c->vh);
+        CKS(ws_get(c, WS_R64, sz, &r64));
+        CKS(ws_get(c, WS_AX64, sz, &ax64));
+        CKS(ws_get(c, WS_TE64, sz, &te64));
+        CKS(ws_get(c, WS_MID64, sz, &mid64));
+        CKS((norm2_dev<P64, NC>(c, w[q].b64, st, &bb[q])));
+        infos[q] = tm_solve_info{};
+        if (!(bb[q] > 0)) { CK(cudaMemsetAsync(w[q].x64, 0, sz, st)); done[q] = 1; continue; }
+        CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
+        if (rr[q] <= tol * tol * bb[q]) { done[q] = 1; continue; }
+        if (PS != P64) {
+            CK((launch_convert<PS, P64, NC, 1>(vb1(c, w[q].rs, r64), nblk(c->vh, BLAS_BS), st)));
+            CK(cudaMemsetAsync(w[q].xs, 0, spinor_bytes(P32, NC, c->vh), st));
+        } else {
+            w[q].rs = r64;
+        }
+        SolverCtl& h = *c->h_ctl;
+        std::memset(&h, 0, sizeof(SolverCtl));
+        h.rr = h.rr_old = rr[q];
+        h.maxiter = maxiter;
+        h.stop_rr = std::max(tol * tol * bb[q], delta * delta * rr[q]);
+        h.flag = CTL_RUN;
+        CKS(put_ctl(c, st));
+    }
+    // batched tables (problems that are already done keep flag != RUN and skip)
+    OpBatch<MAXP> k1{}, k2a{}, k1b{}, k2b{};
+    VecBatch<MAXP> pu{}, up{};
+    int s1, s2;
+    normal_signs(op, &s1, &s2);
+    int ob = 0, vbk = 0;
+    for (int q = 0; q < n; ++q) {
+        tm_ctx* c = cs[q];
+        const int nbd = nblk(c->vh, DSLASH_BS), nbb = nblk(c->vh, BLAS_BS);
+        SolverCtl* ctl = c->ctl;
+        k1.blk_start[q] = k2a.blk_start[q] = k1b.blk_start[q] = k2b.blk_start[q] = ob;
+        pu.blk_start[q] = up.blk_start[q] = vbk;
+        k1.p[q] = make_prob(c, PS, 1, K1_EO_INV, s1, w[q].tes, w[q].ps, nullptr, ctl, false);
+        k2a.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s1, w[q].mids, w[q].tes, w[q].ps, ctl, true);
+        k1b.p[q] = make_prob(c, PS, 1, K1_EO_INV, s2, w[q].tes, w[q].mids, nullptr, ctl, false);
+        k2b.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s2, w[q].aps, w[q].tes, w[q].mids, ctl, false);
+        VecBatch<1> a = vb1(c, w[q].ps, w[q].rs);
+        pu.p[q] = a.p[0];
+        VecBatch<1> u = vb1(c, w[q].xs, w[q].ps, w[q].rs, w[q].aps);
+        up.p[q] = u.p[0];
+        if (done[q]) {   // done problems: a control word that stays stopped
+            c->h_ctl->flag = CTL_STOP;
+            CKS(put_ctl(c, st));
+        }
+        ob += nbd;
+        vbk += nbb;
+    }
+    for (auto* t : {&k1, &k2a, &k1b, &k2b}) { t->n = n; t->blk_start[n] = ob; t->fin = FIN_NONE; }
+    k2a.fin = FIN_CG_ALPHA;
+    pu.n = up.n = n;
+    pu.blk_start[n] = up.blk_start[n] = vbk;
+    auto iteration = [&]() -> cudaError_t {
+        cudaError_t e = launch_cg_pupdate<PS, NC, MAXP>(pu, vbk, st);
+        if (!e) e = launch_dslash<PS, 1, K1_EO_INV, MAXP>(k1, ob, st);
+        if (!e) e = launch_dslash<PS, 1, K2_OE_LOCAL, MAXP>(k2a, ob, st);
+        if (!e) e = launch_dslash<PS, 1, K1_EO_INV, MAXP>(k1b, ob, st);
+        if (!e) e = launch_dslash<PS, 1, K2_OE_LOCAL, MAXP>(k2b, ob, st);
+        if (!e) e = launch_cg_update<PS, PX, NC, MAXP>(up, vbk, st);
+        return e;
+    };
+    cudaGraphExec_t gexec = nullptr;
+    if (sp->use_graph) {
+        cudaGraph_t graph;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        for (int it = 0; it < chunk; ++it) {
+            cudaError_t e = iteration();
+            if (e != cudaSuccess) {
+                cudaStreamEndCapture(st, &graph);
+                return fail(TM_ERR_CUDA, "capture: %s", cudaGetErrorString(e));
+            }
+        }
+        CK(cudaStreamEndCapture(st, &graph));
+        CK(cudaGraphInstantiate(&gexec, graph, 0));
+        cudaGraphDestroy(graph);
+    }
+    tm_status worst = TM_OK;
+    int remaining = 0;
+    for (int q = 0; q < n; ++q) remaining += !done[q];
+    while (remaining > 0) {
+        if (gexec) CK(cudaGraphLaunch(gexec, st));
+        else for (int it = 0; it < chunk; ++it) CK(iteration());
+        for (int q = 0; q < n; ++q) {
+            if (done[q]) continue;
+            tm_ctx* c = cs[q];
+            CKS(get_ctl(c, st));
+            SolverCtl& h = *c->h_ctl;
+            if (h.flag == CTL_RUN) continue;
+            infos[q].iters = h.iter;
+            if (h.flag == CTL_BREAKDOWN) {
+                infos[q].status = TM_ERR_BREAKDOWN; done[q] = 1; --remaining; worst = TM_ERR_BREAKDOWN;
+                continue;
+            }
+            const int nbq = nblk(c->vh, BLAS_BS);
+            if (PS != P64) {
+                CK((launch_add_to64<P32, NC, 1>(vb1(c, w[q].x64, w[q].xs), nbq, st)));
+                CK(cudaMemsetAsync(w[q].xs, 0, spinor_bytes(P32, NC, c->vh), st));
+            }
+            void *r64 = c->ws[WS_R64].first, *ax64 = c->ws[WS_AX64].first, *te64 = c->ws[WS_TE64].first,
+                 *mid64 = c->ws[WS_MID64].first;
+            const int saved_flag = h.flag;
+            const double rr_old = h.rr_old;
+            const int iters = h.iter;
+            CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
+            infos[q].reliable_updates += 1;
+            // true_residual overwrote h.shift only; restore the control word
+            h.flag = saved_flag;
+            if (rr[q] <= tol * tol * bb[q] || saved_flag == CTL_MAXITER || iters >= maxiter ||
+                !std::isfinite(rr[q])) {
+                infos[q].status = rr[q] <= tol * tol * bb[q] ? TM_OK
+                                  : (std::isfinite(rr[q]) ? TM_ERR_NOT_CONVERGED : TM_ERR_BREAKDOWN);
+                if (infos[q].status != TM_OK && worst == TM_OK) worst = (tm_status)infos[q].status;
+                done[q] = 1;
+                --remaining;
+                h.flag = CTL_STOP;
+                CKS(put_ctl(c, st));
+                continue;
+            }
+            if (PS != P64) CK((launch_convert<PS, P64, NC, 1>(vb1(c, w[q].rs, r64), nbq, st)));
+            h.beta = rr[q] / rr_old;
+            h.rr = rr[q];
+            h.iter = iters;
+            h.shift = 0.0;
+            h.stop_rr = std::max(tol * tol * bb[q], delta * delta * rr[q]);
+            h.flag = CTL_RUN;
+            CKS(put_ctl(c, st));
+        }
+    }
+    if (gexec) cudaGraphExecDestroy(gexec);
+    for (int q = 0; q < n; ++q) infos[q].true_rel_res = bb[q] > 0 ? std::sqrt(rr[q] / bb[q]) : 0.0;
+    return worst;
+}
+
+extern "C" tm_status tm_solve_batch(tm_ctx** cs, int n, tm_op op, const tm_solve_params* sp, double** x,
+                                    const double** b, tm_solve_info* infos, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!cs || !sp || !x || !b || !infos || n < 1 || n > MAXP) return fail(TM_ERR_ARG, "tm_solve_batch: bad argument");
+    if (op != TM_MDAGM && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_solve_batch: light normal operators only");
+    CKS(check_prec(sp->sloppy));
+    for (int q = 0; q < n; ++q) {
+        if (!cs[q] || !x[q] || !b[q]) return fail(TM_ERR_ARG, "tm_solve_batch: null problem %d", q);
+        if (cs[q]->device != cs[0]->device) return fail(TM_ERR_ARG, "tm_solve_batch: all contexts on one device");
+    }
+    CK(cudaSetDevice(cs[0]->device));
+    const cudaStream_t st = cs[0]->sstream;
+    CKS(enter_solver(cs[0], stream));
+    std::vector<BatchWs> w(n);
+    const int PS = sp->sloppy;
+    for (int q = 0; q < n; ++q) {
+        tm_ctx* c = cs[q];
+        CKS(ensure_prec(c, P64, st));
+        CKS(ensure_prec(c, PS, st));
+        const size_t s64 = spinor_bytes(P64, 12, c->vh), ss = spinor_bytes(PS, 12, c->vh);
+        CKS(ws_get(c, WS_X64, s64, &w[q].x64));
+        CKS(ws_get(c, WS_B64, s64, &w[q].b64));
+        CKS(ws_get(c, WS_P_S, ss, &w[q].ps));
+        CKS(ws_get(c, WS_AP_S, ss, &w[q].aps));
+        if (PS == P64) {
+            CKS(ws_get(c, WS_TE64, s64, &w[q].tes));
+            CKS(ws_get(c, WS_MID_S, ss, &w[q].mids));
+            w[q].xs = w[q].x64;
+            w[q].rs = nullptr;   // set to r64 in batch_core
+        } else {
+            CKS(ws_get(c, WS_TE_S, ss, &w[q].tes));
+            CKS(ws_get(c, WS_MID_S, ss, &w[q].mids));
+            CKS(ws_get(c, WS_R_S, ss, &w[q].rs));
+            CKS(ws_get(c, WS_X_S, spinor_bytes(P32, 12, c->vh), &w[q].xs));
+        }
+        CKS(stage_in(c, 1, b[q], WS_STAGE_B, w[q].b64, st));
+        CKS(stage_in(c, 1, x[q], WS_STAGE_X, w[q].x64, st));
+    }
+    tm_status s;
+    switch (PS) {
+        case P64: {
+            // FP64 batch: the even temporary of the operator must not alias the residual's
+            for (int q = 0; q < n; ++q) CKS(ws_get(cs[q], WS_TE_S, spinor_bytes(P64, 12, cs[q]->vh), &w[q].tes));
+            s = batch_core<P64>(cs, n, op, sp, w, infos, st);
+            break;
+        }
+        case P32: s = batch_core<P32>(cs, n, op, sp, w, infos, st); break;
+        case PB16: s = batch_core<PB16>(cs, n, op, sp, w, infos, st); break;
+        default: s = batch_core<PF16>(cs, n, op, sp, w, infos, st); break;
+    }
+    for (int q = 0; q < n; ++q) CKS(stage_out(cs[q], 1, x[q], WS_STAGE_X, w[q].x64, st));
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int q = 0; q < n; ++q) infos[q].seconds = secs;
+    if (s != TM_OK) fail(s, "tm_solve_batch: at least one problem failed");
+    return s;
+}

@@ -1,0 +1,272 @@
+// Even-odd Schur operator kernels of eq:hQpm (light doublet) and eq:hQh (heavy doublet).
+//
+//   Q_hat psi_o = g5 [ (M_oo) psi_o - M_oe M_ee^-1 M_eo psi_o ],  M_eo = -kappa H_eo
+//
+// is applied in two passes, one thread per output site:
+//   K1 (even output):  t_e = (M_ee)^-1 H_eo psi_o            hop + site-local 6x6 inverse blocks
+//   K2 (odd output):   out = g5 [ M_oo psi_o - kappa^2 H_oe t_e ]   hop + clover/twist + g5
+// K2 can fuse ||out||^2 into a deterministic two-level FP64 reduction whose last
+// block finalises a solver scalar (CG alpha), so a CG iteration needs no separate
+// reduction launch.  Every kernel takes a table of problems (one or a batch of
+// lattices of different volumes); a block belongs to exactly one problem.
+#include "tm_internal.h"
+#include "tm_kernels.h"
+
+namespace tmk {
+
+// ---------------------------------------------------------------------------
+// Spin projection / reconstruction of the chiral basis for one hop.
+//   S = -1: forward  (1 - g_mu) U_mu(x) psi(x+mu)
+//   S = +1: backward (1 + g_mu) U_mu(x-mu)^dagger psi(x-mu)
+// With g_mu = [[0, G],[G^+, 0]] (G_x = -i s1, G_y = -i s2, G_z = -i s3, G_t = -1):
+//   (1 + S g) psi = (h, S G^+ h),  h = psi_up + S G psi_down,
+// so only the two-spin half spinor h is transported by the link.
+// ---------------------------------------------------------------------------
+template <typename R, int MU, int S, bool DAG>
+__device__ __forceinline__ void hop_dir(cpx<R> (&acc)[4][3], const cpx<R>* psi,
+                                        const cpx<R> (&u)[9], R phase) {
+    const R s = (R)S;
+    cpx<R> h0[3], h1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const cpx<R> p0 = psi[c], p1 = psi[3 + c], p2 = psi[6 + c], p3 = psi[9 + c];
+        if (MU == 0) {        // h0 = p0 - s i p3, h1 = p1 - s i p2
+            h0[c] = p0 - s * mul_i(p3);
+            h1[c] = p1 - s * mul_i(p2);
+        } else if (MU == 1) { // h0 = p0 - s p3, h1 = p1 + s p2
+            h0[c] = p0 - s * p3;
+            h1[c] = p1 + s * p2;
+        } else if (MU == 2) { // h0 = p0 - s i p2, h1 = p1 + s i p3
+            h0[c] = p0 - s * mul_i(p2);
+            h1[c] = p1 + s * mul_i(p3);
+        } else {              // h0 = p0 - s p2, h1 = p1 - s p3
+            h0[c] = p0 - s * p2;
+            h1[c] = p1 - s * p3;
+        }
+        if (MU == 3) { h0[c] = phase * h0[c]; h1[c] = phase * h1[c]; }
+    }
+    cpx<R> g0[3], g1[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        g0[a] = C((R)0, (R)0);
+        g1[a] = C((R)0, (R)0);
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            if (DAG) {
+                cfma_cj(g0[a], u[3 * b + a], h0[b]);
+                cfma_cj(g1[a], u[3 * b + a], h1[b]);
+            } else {
+                cfma(g0[a], u[3 * a + b], h0[b]);
+                cfma(g1[a], u[3 * a + b], h1[b]);
+            }
+        }
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        acc[0][a] = acc[0][a] + g0[a];
+        acc[1][a] = acc[1][a] + g1[a];
+        if (MU == 0) {        // lower += s i (g1, g0)
+            acc[2][a] = acc[2][a] + s * mul_i(g1[a]);
+            acc[3][a] = acc[3][a] + s * mul_i(g0[a]);
+        } else if (MU == 1) { // lower += s (g1, -g0)
+            acc[2][a] = acc[2][a] + s * g1[a];
+            acc[3][a] = acc[3][a] - s * g0[a];
+        } else if (MU == 2) { // lower += s i (g0, -g1)
+            acc[2][a] = acc[2][a] + s * mul_i(g0[a]);
+            acc[3][a] = acc[3][a] - s * mul_i(g1[a]);
+        } else {              // lower += -s (g0, g1)
+            acc[2][a] = acc[2][a] - s * g0[a];
+            acc[3][a] = acc[3][a] - s * g1[a];
+        }
+    }
+}
+
+// All 8 hops for NF flavours into acc[NF][4][3]; output site (c, i) of parity po.
+template <int P, int NF, int MU>
+__device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], const OpProb& pr,
+                                       const Coord& c, long i, int po) {
+    using R = typename PT<P>::R;
+    const Geom& g = pr.g;
+    int xf = c.x, yf = c.y, zf = c.z, tf = c.t;
+    int xb = c.x, yb = c.y, zb = c.z, tb = c.t;
+    R ph_f = (R)1, ph_b = (R)1;
+    if (MU == 0) { xf = (c.x + 1 == g.X) ? 0 : c.x + 1; xb = (c.x == 0) ? g.X - 1 : c.x - 1; }
+    if (MU == 1) { yf = (c.y + 1 == g.Y) ? 0 : c.y + 1; yb = (c.y == 0) ? g.Y - 1 : c.y - 1; }
+    if (MU == 2) { zf = (c.z + 1 == g.Z) ? 0 : c.z + 1; zb = (c.z == 0) ? g.Z - 1 : c.z - 1; }
+    if (MU == 3) {
+        if (c.t + 1 == g.T) { tf = 0; ph_f = (R)pr.bc_t; } else tf = c.t + 1;
+        if (c.t == 0) { tb = g.T - 1; ph_b = (R)pr.bc_t; } else tb = c.t - 1;
+    }
+    const long nf = cb_index(g, xf, yf, zf, tf);
+    const long nb = cb_index(g, xb, yb, zb, tb);
+    cpx<R> u[9];
+    cpx<R> psi[NF * 12];
+    // forward
+    load_spinor<P, NF * 12>(pr.in, g.vh, nf, psi);
+    load_link<P>(pr.gauge[po], g.vh, MU, i, u);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false>(acc[f], psi + 12 * f, u, ph_f);
+    // backward
+    load_spinor<P, NF * 12>(pr.in, g.vh, nb, psi);
+    load_link<P>(pr.gauge[1 - po], g.vh, MU, nb, u);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true>(acc[f], psi + 12 * f, u, ph_b);
+}
+
+// w = B v (CONJ: B^dagger v) for a full complex 6x6 block stored row major.
+template <typename R, bool CONJ>
+__device__ __forceinline__ void full6_mv(cpx<R> (&w)[6], const R* m, const cpx<R> (&v)[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) w[r] = C((R)0, (R)0);
+#pragma unroll
+    for (int r = 0; r < 6; ++r)
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            const cpx<R> e = C(m[2 * (6 * r + j)], m[2 * (6 * r + j) + 1]);
+            if (CONJ) cfma_cj(w[j], e, v[r]);   // (B^+)_{j r} = conj(B_{r j})
+            else cfma(w[r], e, v[j]);
+        }
+}
+
+// w += H v for a packed hermitian 6x6 block (36 reals).
+template <typename R>
+__device__ __forceinline__ void herm6_mv_acc(cpx<R> (&w)[6], const R* m, const cpx<R> (&v)[6]) {
+#pragma unroll
+    for (int r = 0; r < 6; ++r) w[r] = w[r] + m[r] * v[r];
+#pragma unroll
+    for (int r = 1; r < 6; ++r)
+#pragma unroll
+        for (int j = 0; j < r; ++j) {
+            const cpx<R> e = C(m[herm_off(r, j)], m[herm_off(r, j) + 1]);
+            cfma(w[r], e, v[j]);      // lower:  H_rj v_j
+            cfma_cj(w[j], e, v[r]);   // upper:  H_jr = conj(H_rj)
+        }
+}
+
+template <int P, int NF, int KIND, int NP, int BS>
+__global__ void __launch_bounds__(BS) dslash_kernel(const __grid_constant__ OpBatch<NP> b) {
+    using R = typename PT<P>::R;
+    __shared__ double sh[BS / 32];
+    const int k = find_problem<NP>(b, blockIdx.x);
+    const OpProb& pr = b.p[k];
+    if (pr.ctl != nullptr && pr.ctl->flag != CTL_RUN) return;
+    const int lb = blockIdx.x - b.blk_start[k];
+    const long i = (long)lb * BS + threadIdx.x;
+    const bool valid = i < pr.g.vh;
+    const int po = (KIND == K1_EO_INV) ? 0 : 1;   // output parity
+    double nrm = 0.0;
+    if (valid) {
+        const Coord c = cb_coords(pr.g, i, po);
+        cpx<R> acc[NF][4][3];
+#pragma unroll
+        for (int f = 0; f < NF; ++f)
+#pragma unroll
+            for (int s = 0; s < 4; ++s)
+#pragma unroll
+                for (int a = 0; a < 3; ++a) acc[f][s][a] = C((R)0, (R)0);
+        hop_mu<P, NF, 0>(acc, pr, c, i, po);
+        hop_mu<P, NF, 1>(acc, pr, c, i, po);
+        hop_mu<P, NF, 2>(acc, pr, c, i, po);
+        hop_mu<P, NF, 3>(acc, pr, c, i, po);
+
+        cpx<R> out[NF * 12];
+        if constexpr (KIND == K1_EO_INV) {
+            if constexpr (NF == 1) {
+                // t_e = (A_c + i sign s_c mu_t)^-1 (H psi) per chirality block c
+#pragma unroll
+                for (int cb = 0; cb < 2; ++cb) {
+                    cpx<R> v[6], w[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) v[j] = acc[0][2 * cb + j / 3][j % 3];
+                    R m[72];
+                    load_reals<P, 72>(pr.clov, pr.g.vh, i, 72 * cb, m);
+                    if (pr.sign > 0) full6_mv<R, false>(w, m, v);
+                    else full6_mv<R, true>(w, m, v);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
+                }
+            } else {
+                // heavy: [[P, E],[E, P^+]] (sign +) or [[P^+, E],[E, P]] (sign -)
+                R e[72];
+                load_reals<P, 72>(pr.clov, pr.g.vh, i, 144, e);
+#pragma unroll
+                for (int cb = 0; cb < 2; ++cb) {
+                    cpx<R> vu[6], vd[6], wu[6], wd[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        vu[j] = acc[0][2 * cb + j / 3][j % 3];
+                        vd[j] = acc[NF - 1][2 * cb + j / 3][j % 3];
+                    }
+                    R m[72];
+                    load_reals<P, 72>(pr.clov, pr.g.vh, i, 72 * cb, m);
+                    if (pr.sign > 0) { full6_mv<R, false>(wu, m, vu); full6_mv<R, true>(wd, m, vd); }
+                    else { full6_mv<R, true>(wu, m, vu); full6_mv<R, false>(wd, m, vd); }
+                    herm6_mv_acc<R>(wu, e + 36 * cb, vd);
+                    herm6_mv_acc<R>(wd, e + 36 * cb, vu);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
+                }
+            }
+        } else {
+            // out = g5 [ (A + i tw g5 [tau3]) psi - eps tau1 psi - kappa^2 acc ]
+            cpx<R> psi[NF * 12];
+            load_spinor<P, NF * 12>(pr.loc, pr.g.vh, i, psi);
+            R m[72];
+            load_reals<P, 72>(pr.clov, pr.g.vh, i, 0, m);
+            const R k2 = (R)(pr.kappa * pr.kappa);
+            const R tw = (R)pr.tw;
+            const R eps = (R)pr.eps;
+#pragma unroll
+            for (int f = 0; f < NF; ++f) {
+                const R t3 = (f == 0) ? (R)1 : (R)-1;
+#pragma unroll
+                for (int cb = 0; cb < 2; ++cb) {
+                    const R sc = (cb == 0) ? (R)1 : (R)-1;
+                    cpx<R> v[6], w[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        v[j] = psi[12 * f + 6 * cb + j];
+                        w[j] = (tw * sc * t3) * mul_i(v[j]);
+                        if constexpr (NF == 2) w[j] = w[j] - eps * psi[12 * (1 - f) + 6 * cb + j];
+                        w[j] = w[j] - k2 * acc[f][2 * cb + j / 3][j % 3];
+                    }
+                    herm6_mv_acc<R>(w, m + 36 * cb, v);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) out[12 * f + 6 * cb + j] = (cb == 0) ? w[j] : -w[j];
+                }
+            }
+            if (pr.partial != nullptr) {
+                R s = (R)0;
+#pragma unroll
+                for (int q = 0; q < NF * 12; ++q) s += norm2(out[q]);
+                nrm = (double)s;
+            }
+        }
+        store_spinor<P, NF * 12>(pr.out, pr.g.vh, i, out);
+    }
+    if constexpr (KIND == K2_OE_LOCAL) {
+      if (pr.partial != nullptr) {
+        const double bs = block_sum<BS>(nrm, sh);
+        reduce_finalize<BS>(pr.partial, pr.counter, pr.nblk, lb, bs, b.fin, pr.ctl, pr.ms,
+                            nullptr, sh);
+      }
+    }
+}
+
+template <int P, int NF, int KIND, int NP>
+cudaError_t launch_dslash(const OpBatch<NP>& b, int nblocks, cudaStream_t st) {
+    dslash_kernel<P, NF, KIND, NP, DSLASH_BS><<<nblocks, DSLASH_BS, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+#define TM_INST(P, NF, KIND, NP) \
+    template cudaError_t launch_dslash<P, NF, KIND, NP>(const OpBatch<NP>&, int, cudaStream_t);
+#define TM_INST_P(P)                                                                      \
+    TM_INST(P, 1, K1_EO_INV, 1) TM_INST(P, 1, K2_OE_LOCAL, 1) TM_INST(P, 2, K1_EO_INV, 1) \
+    TM_INST(P, 2, K2_OE_LOCAL, 1) TM_INST(P, 1, K1_EO_INV, MAXP) TM_INST(P, 1, K2_OE_LOCAL, MAXP)
+TM_INST_P(P64)
+TM_INST_P(P32)
+TM_INST_P(PB16)
+TM_INST_P(PF16)
+
+}  // namespace tmk

@@ -1,0 +1,50 @@
+// Host-side context of the C ABI: device copies of the gauge field and clover
+// terms per storage precision, the gauge-state generation counter (Sec. 3's
+// gauge_id cascade), reduction scratch and solver workspace.
+#pragma once
+
+#include <map>
+#include <string>
+
+#include "tm_internal.h"
+#include "tm_kernels.h"
+
+struct tm_ctx {
+    int device = 0;
+    tmk::Geom g{};
+    long vh = 0;
+    cudaStream_t sstream = nullptr;   // private stream for solver work (graph capture)
+
+    // gauge state (Sec. 3: tm_GaugeState_t / update_tm_gauge_id)
+    double gauge_id = 0.0;
+    long gauge_gen = 0;                // 0 = no gauge loaded
+    void* gauge64[2] = {nullptr, nullptr};
+    void* gaugeP[4][2] = {};
+    long gaugeP_gen[4] = {0, 0, 0, 0};
+
+    // clover state: computed for (gauge_gen, params)
+    tm_params params{};
+    long clover_gauge_gen = -1;
+    long clover_stamp = 0;
+    bool have_heavy = false;
+    double* clovA64[2] = {nullptr, nullptr};
+    double* clovB64 = nullptr;
+    double* clovH64 = nullptr;
+    void* clovAP[4] = {};
+    void* clovBP[4] = {};
+    void* clovHP[4] = {};
+    long clovP_stamp[4] = {0, 0, 0, 0};
+
+    // reduction scratch and control words
+    double* partial = nullptr;
+    unsigned int* counter = nullptr;
+    int max_blocks = 0;
+    tmk::SolverCtl* ctl = nullptr;
+    tmk::MsCtl* ms = nullptr;
+    tmk::SolverCtl* h_ctl = nullptr;   // pinned mirrors
+    tmk::MsCtl* h_ms = nullptr;
+    double* d_scal = nullptr;          // 16 FP64 reduction results
+    double* h_scal = nullptr;
+
+    std::map<int, std::pair<void*, size_t>> ws;   // workspace buffers by id
+};

@@ -1,0 +1,213 @@
+"""Thin ctypes binding of include/tm.h (argument marshalling only).
+
+Every function has the C name and returns what the C call fills in; a non-zero
+tm_status raises TMError carrying the status and tm_last_error().  Pointers may
+be given as torch tensors, numpy arrays, ctypes objects or plain integers.
+Streams default to torch's current CUDA stream.  There is no fallback: if the
+shared library cannot be loaded, importing this module raises.
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libtm.so")
+
+TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM, TM_ERR_STALE, TM_ERR_NOT_CONVERGED, \
+    TM_ERR_BREAKDOWN, TM_ERR_TIMEOUT, TM_ERR_UNSUPPORTED = range(9)
+TM_F64, TM_F32, TM_BF16, TM_F16 = range(4)
+TM_QHAT_PLUS, TM_QHAT_MINUS, TM_MDAGM, TM_QPQM, TM_QH, TM_QH_DAG, TM_QH_SQ = range(7)
+
+PREC_NAMES = {TM_F64: "f64", TM_F32: "f32", TM_BF16: "bf16", TM_F16: "f16"}
+STATUS_NAMES = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_CUDA", 3: "TM_ERR_OOM", 4: "TM_ERR_STALE",
+                5: "TM_ERR_NOT_CONVERGED", 6: "TM_ERR_BREAKDOWN", 7: "TM_ERR_TIMEOUT",
+                8: "TM_ERR_UNSUPPORTED"}
+
+
+class tm_params(ct.Structure):
+    _fields_ = [("kappa", ct.c_double), ("csw", ct.c_double), ("mu", ct.c_double),
+                ("mubar", ct.c_double), ("epsbar", ct.c_double), ("bc_t", ct.c_int)]
+
+
+class tm_solve_params(ct.Structure):
+    _fields_ = [("tol", ct.c_double), ("maxiter", ct.c_int), ("sloppy", ct.c_int),
+                ("delta", ct.c_double), ("chunk", ct.c_int), ("use_graph", ct.c_int)]
+
+
+class tm_solve_info(ct.Structure):
+    _fields_ = [("iters", ct.c_int), ("reliable_updates", ct.c_int), ("status", ct.c_int),
+                ("true_rel_res", ct.c_double), ("seconds", ct.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TMError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with python -m paper_2212_06635_gb300.build")
+    return ct.CDLL(LIB_PATH)
+
+
+lib = _load()
+_vp = ct.c_void_p
+_sigs = {
+    "tm_create": [ct.POINTER(_vp), ct.POINTER(ct.c_int), ct.c_int],
+    "tm_destroy": [_vp],
+    "tm_gauge_load": [_vp, _vp, ct.c_double, _vp],
+    "tm_gauge_id": [_vp, ct.POINTER(ct.c_double)],
+    "tm_clover_compute": [_vp, ct.POINTER(tm_params), _vp],
+    "tm_clover_export": [_vp, ct.c_int, _vp, _vp],
+    "tm_field_bytes": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_size_t)],
+    "tm_field_import": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_field_export": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_apply_Mhat": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_solve_cg": [_vp, ct.c_int, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
+    "tm_solve_multishift": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(_vp), _vp,
+                            ct.POINTER(tm_solve_params), ct.POINTER(tm_solve_info), _vp],
+    "tm_solve_batch": [ct.POINTER(_vp), ct.c_int, ct.c_int, ct.POINTER(tm_solve_params), ct.POINTER(_vp),
+                       ct.POINTER(_vp), ct.POINTER(tm_solve_info), _vp],
+    "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
+}
+for _n, _a in _sigs.items():
+    getattr(lib, _n).argtypes = _a
+    getattr(lib, _n).restype = ct.c_int
+lib.tm_last_error.argtypes = []
+lib.tm_last_error.restype = ct.c_char_p
+
+EXPORTED = list(_sigs) + ["tm_last_error"]
+
+
+def tm_last_error() -> str:
+    return lib.tm_last_error().decode()
+
+
+def _check(status):
+    if status != TM_OK:
+        raise TMError(status, tm_last_error())
+
+
+def ptr(x):
+    """Address of a tensor / array / ctypes object / int."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C contiguous")
+        return x.ctypes.data
+    return ct.addressof(x)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return torch.cuda.current_stream().cuda_stream
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return stream.cuda_stream
+    return stream
+
+
+def tm_create(dims, device=0):
+    h = _vp()
+    d = (ct.c_int * 4)(*[int(v) for v in dims])
+    _check(lib.tm_create(ct.byref(h), d, int(device)))
+    return h.value
+
+
+def tm_destroy(ctx):
+    _check(lib.tm_destroy(ctx))
+
+
+def tm_gauge_load(ctx, links, gauge_id=0.0, stream=None):
+    _check(lib.tm_gauge_load(ctx, ptr(links), float(gauge_id), _stream(stream)))
+
+
+def tm_gauge_id(ctx):
+    v = ct.c_double()
+    _check(lib.tm_gauge_id(ctx, ct.byref(v)))
+    return v.value
+
+
+def tm_clover_compute(ctx, kappa, csw, mu=0.0, mubar=0.0, epsbar=0.0, bc_t=-1, stream=None):
+    p = tm_params(kappa, csw, mu, mubar, epsbar, int(bc_t))
+    _check(lib.tm_clover_compute(ctx, ct.byref(p), _stream(stream)))
+
+
+def tm_clover_export(ctx, parity, out, stream=None):
+    _check(lib.tm_clover_export(ctx, int(parity), ptr(out), _stream(stream)))
+
+
+def tm_field_bytes(ctx, prec, nflavour=1):
+    n = ct.c_size_t()
+    _check(lib.tm_field_bytes(ctx, int(prec), int(nflavour), ct.byref(n)))
+    return n.value
+
+
+def tm_field_import(ctx, prec, nflavour, dst, src, stream=None):
+    _check(lib.tm_field_import(ctx, int(prec), int(nflavour), ptr(dst), ptr(src), _stream(stream)))
+
+
+def tm_field_export(ctx, prec, nflavour, dst, src, stream=None):
+    _check(lib.tm_field_export(ctx, int(prec), int(nflavour), ptr(dst), ptr(src), _stream(stream)))
+
+
+def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
+    _check(lib.tm_apply_Mhat(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
+
+
+def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.1, chunk=16, use_graph=1):
+    return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph)
+
+
+def tm_solve_cg(ctx, op, sp, x, b, stream=None, check=True):
+    info = tm_solve_info()
+    st = lib.tm_solve_cg(ctx, int(op), ct.byref(sp), ptr(x), ptr(b), ct.byref(info), _stream(stream))
+    if check:
+        _check(st)
+    return info
+
+
+def tm_solve_multishift(ctx, op, shifts, xs, b, sp, stream=None, check=True):
+    n = len(shifts)
+    sh = (ct.c_double * n)(*shifts)
+    xp = (_vp * n)(*[ptr(x) for x in xs])
+    infos = (tm_solve_info * n)()
+    st = lib.tm_solve_multishift(ctx, int(op), n, sh, xp, ptr(b), ct.byref(sp), infos, _stream(stream))
+    if check:
+        _check(st)
+    return list(infos)
+
+
+def tm_solve_batch(ctxs, op, sp, xs, bs, stream=None, check=True):
+    n = len(ctxs)
+    cp = (_vp * n)(*ctxs)
+    xp = (_vp * n)(*[ptr(x) for x in xs])
+    bp = (_vp * n)(*[ptr(b) for b in bs])
+    infos = (tm_solve_info * n)()
+    st = lib.tm_solve_batch(cp, n, int(op), ct.byref(sp), xp, bp, infos, _stream(stream))
+    if check:
+        _check(st)
+    return list(infos)
+
+
+def tm_power_iteration(ctx, op, iters=100, stream=None):
+    v = ct.c_double()
+    _check(lib.tm_power_iteration(ctx, int(op), int(iters), ct.byref(v), _stream(stream)))
+    return v.value

@@ -1,0 +1,92 @@
+"""Parity of the CUDA operators (clover term, Q_hat_pm of eq:hQpm, Q_hat_h of
+eq:hQh and their normal products) against the FP64 CPU oracle, element by
+element, in every storage precision."""
+import numpy as np
+import pytest
+
+from oracle import dirac as D
+from synth import fields as F
+from tests.gpu_util import PREC_TOL, Lat, rel
+
+pytestmark = pytest.mark.gpu
+
+KAPPA, CSW, MU, MUBAR, EPSBAR = 0.1394, 1.69, 0.01, 0.1246, 0.1350
+# lattices spanning several 128-site tiles with ragged tails, plus the minimum 2^4
+DIMS = [(4, 4, 4, 4), (6, 4, 4, 6), (2, 2, 2, 2), (8, 6, 4, 10)]
+
+
+@pytest.fixture(scope="module", params=DIMS, ids=lambda d: "x".join(map(str, d)))
+def setup(request):
+    dims = request.param
+    u = F.gauge_field(dims, 1000 + sum(dims))
+    op = D.TwistedMassClover(u, dims, KAPPA, CSW, mu=MU, mubar=MUBAR, epsbar=EPSBAR)
+    lat = Lat(u, dims, KAPPA, CSW, mu=MU, mubar=MUBAR, epsbar=EPSBAR)
+    yield dims, op, lat
+    lat.close()
+
+
+def test_clover_term_fp64(setup):
+    import torch
+    dims, op, lat = setup
+    vh = lat.vh
+    for par, sites in ((0, op.geo.even), (1, op.geo.odd)):
+        out = torch.empty(vh * 2 * 36 * 2, dtype=torch.float64, device="cuda:0")
+        lat.tm.tm_clover_export(lat.ctx, par, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.complex128).reshape(vh, 2, 6, 6)
+        A = op.A[sites]
+        ref = np.stack([A[:, :6, :6], A[:, 6:, 6:]], axis=1)
+        assert rel(got, ref) < 1e-14
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3, 2], ids=["f64", "f32", "f16", "bf16"])
+def test_light_schur_operators(setup, prec):
+    dims, op, lat = setup
+    tm = lat.tm
+    psi = F.odd_spinor(dims, 7)
+    for code, ref in ((tm.TM_QHAT_PLUS, op.Qhat(psi, +1)), (tm.TM_QHAT_MINUS, op.Qhat(psi, -1)),
+                      (tm.TM_MDAGM, op.MdagM(psi)), (tm.TM_QPQM, op.QpQm(psi))):
+        got = lat.apply(code, prec, psi)
+        assert rel(got, ref) < PREC_TOL[prec], (code, rel(got, ref))
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3, 2], ids=["f64", "f32", "f16", "bf16"])
+def test_heavy_schur_operators(setup, prec):
+    dims, op, lat = setup
+    tm = lat.tm
+    psi = F.odd_spinor(dims, 8, 2)
+    for code, ref in ((tm.TM_QH, op.Qhat_heavy(psi, +1)), (tm.TM_QH_DAG, op.Qhat_heavy(psi, -1)),
+                      (tm.TM_QH_SQ, op.heavy_sq(psi))):
+        got = lat.apply(code, prec, psi)
+        assert rel(got, ref) < PREC_TOL[prec], (code, rel(got, ref))
+
+
+def test_periodic_time_boundary():
+    dims = (4, 4, 2, 6)
+    u = F.gauge_field(dims, 31)
+    op = D.TwistedMassClover(u, dims, KAPPA, CSW, mu=MU, bc_t=+1)
+    lat = Lat(u, dims, KAPPA, CSW, mu=MU, bc_t=+1)
+    try:
+        psi = F.odd_spinor(dims, 32)
+        assert rel(lat.apply(lat.tm.TM_QHAT_PLUS, 0, psi), op.Qhat(psi, +1)) < 1e-13
+    finally:
+        lat.close()
+
+
+def test_full_size_sampled_32x64():
+    """32^3x64 (the mixed-precision CG workload) in the launch configuration the
+    benchmark uses: FP64 and FP32 Q_hat_+ checked at sampled odd sites."""
+    dims = (32, 32, 32, 64)
+    u = F.gauge_field(dims, 1001)
+    op = D.TwistedMassClover(u, dims, 0.1400, CSW, mu=0.0015)
+    lat = Lat(u, dims, 0.1400, CSW, mu=0.0015)
+    try:
+        psi = F.odd_spinor(dims, 2001)
+        rng = np.random.default_rng(5)
+        s = np.unique(np.concatenate([[0, 1, lat.vh - 1], rng.integers(0, lat.vh, 64)]))
+        ref = op.Qhat_at(psi, s, +1)
+        for prec in (0, 1):
+            got = lat.apply(lat.tm.TM_QHAT_PLUS, prec, psi)[s]
+            assert rel(got, ref) < PREC_TOL[prec], (prec, rel(got, ref))
+    finally:
+        lat.close()
