@@ -122,7 +122,9 @@ tm_status tm_clover_export(tm_ctx* ctx, int parity, double* out, void* stream);
 
 /* Bytes of one native odd-site field: nflavour 1 (light) or 2 (heavy). */
 tm_status tm_field_bytes(const tm_ctx* ctx, tm_prec prec, int nflavour, size_t* bytes);
-/* canonical FP64 (device) <-> native (device).  Both pointers 16-byte aligned. */
+/* canonical FP64 <-> native (device).  The canonical pointer may be a host
+ * pointer (detected; copied through a library-owned device staging buffer, and
+ * the call then synchronises `stream`) or a device pointer.  16-byte aligned. */
 tm_status tm_field_import(tm_ctx* ctx, tm_prec prec, int nflavour, void* dst_native,
                           const double* src_canonical, void* stream);
 tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_canonical,
@@ -157,6 +159,15 @@ tm_status tm_solve_batch(tm_ctx** ctxs, int n, tm_op op, const tm_solve_params* 
 /* Largest eigenvalue of the HPD op (TM_MDAGM, TM_QPQM, TM_QH_SQ) by `iters` power
  * iterations from a fixed seeded start vector, FP64. */
 tm_status tm_power_iteration(tm_ctx* ctx, tm_op op, int iters, double* lambda_max, void* stream);
+
+/* Average device time per launch of the two passes of one Schur operator in
+ * storage precision prec (op = TM_QHAT_PLUS / TM_QHAT_MINUS / TM_QH / TM_QH_DAG):
+ * ms[0] = even pass (hop + inverse blocks, eq:hQpm's (M_ee)^-1 M_eo),
+ * ms[1] = odd pass (hop + clover + twist + g5).  Each pass is launched `reps`
+ * times back to back between CUDA events recorded on `stream`; `in` is a native
+ * field of precision prec, outputs go to library-owned scratch. */
+tm_status tm_kernel_times(tm_ctx* ctx, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
+                          void* stream);
 
 /* Message of the calling thread's last failure ("" if none). */
 const char* tm_last_error(void);

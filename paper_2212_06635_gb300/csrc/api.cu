@@ -89,7 +89,7 @@ static tm_status ws_get(tm_ctx* c, int id, size_t bytes, void** out) {
 enum WsId {
     WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
-    WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID,
+    WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO,
     WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
 };
 
@@ -413,7 +413,17 @@ extern "C" tm_status tm_field_import(tm_ctx* c, tm_prec prec, int nf, void* dst,
     if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_import: pointers must be 16-byte aligned");
     CKS(check_prec(prec));
     CK(cudaSetDevice(c->device));
-    CK(import_any(prec, nf, dst, src, c->vh, S(stream)));
+    const cudaStream_t st = S(stream);
+    if (is_device_ptr(src)) {
+        CK(import_any(prec, nf, dst, src, c->vh, st));
+        return TM_OK;
+    }
+    const size_t bytes = sizeof(double) * 24 * nf * c->vh;
+    void* stage = nullptr;
+    CKS(ws_get(c, WS_STAGE_IO, bytes, &stage));
+    CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
+    CK(import_any(prec, nf, dst, reinterpret_cast<const double*>(stage), c->vh, st));
+    CK(cudaStreamSynchronize(st));
     return TM_OK;
 }
 
@@ -422,8 +432,78 @@ extern "C" tm_status tm_field_export(tm_ctx* c, tm_prec prec, int nf, double* ds
     if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_export: pointers must be 16-byte aligned");
     CKS(check_prec(prec));
     CK(cudaSetDevice(c->device));
-    CK(export_any(prec, nf, dst, src, c->vh, S(stream)));
+    const cudaStream_t st = S(stream);
+    if (is_device_ptr(dst)) {
+        CK(export_any(prec, nf, dst, src, c->vh, st));
+        return TM_OK;
+    }
+    const size_t bytes = sizeof(double) * 24 * nf * c->vh;
+    void* stage = nullptr;
+    CKS(ws_get(c, WS_STAGE_IO, bytes, &stage));
+    CK(export_any(prec, nf, reinterpret_cast<double*>(stage), src, c->vh, st));
+    CK(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
     return TM_OK;
+}
+
+template <int P, int NF>
+static tm_status kernel_times_t(tm_ctx* c, int sign, const void* in, int reps, double* ms, cudaStream_t st) {
+    void *te = nullptr, *out = nullptr;
+    CKS(ws_get(c, WS_APPLY_TE, spinor_bytes(P, 12 * NF, c->vh), &te));
+    CKS(ws_get(c, WS_APPLY_MID, spinor_bytes(P, 12 * NF, c->vh), &out));
+    OpBatch<1> b{};
+    b.n = 1;
+    b.fin = FIN_NONE;
+    const int nb = nblk(c->vh, DSLASH_BS);
+    b.blk_start[0] = 0;
+    b.blk_start[1] = nb;
+    cudaEvent_t e0, e1, e2;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    CK(cudaEventCreate(&e2));
+    b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, nullptr, false);
+    CK((launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st)));   // warm-up
+    CK(cudaEventRecord(e0, st));
+    for (int r = 0; r < reps; ++r) CK((launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st)));
+    CK(cudaEventRecord(e1, st));
+    b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, nullptr, false);
+    for (int r = 0; r < reps; ++r) CK((launch_dslash<P, NF, K2_OE_LOCAL, 1>(b, nb, st)));
+    CK(cudaEventRecord(e2, st));
+    CK(cudaEventSynchronize(e2));
+    float t1 = 0, t2 = 0;
+    CK(cudaEventElapsedTime(&t1, e0, e1));
+    CK(cudaEventElapsedTime(&t2, e1, e2));
+    ms[0] = t1 / reps;
+    ms[1] = t2 / reps;
+    cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
+                                     void* stream) {
+    if (!c || !in || !ms || reps < 1) return fail(TM_ERR_ARG, "tm_kernel_times: bad argument");
+    if (op != TM_QHAT_PLUS && op != TM_QHAT_MINUS && op != TM_QH && op != TM_QH_DAG)
+        return fail(TM_ERR_ARG, "tm_kernel_times: op must be a single Schur operator");
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ensure_prec(c, prec, st));
+    const int sign = (op == TM_QHAT_PLUS || op == TM_QH) ? +1 : -1;
+    if (nflav(op) == 2) {
+        if (!c->have_heavy) return fail(TM_ERR_ARG, "tm_kernel_times: no heavy clover term");
+        switch (prec) {
+            case TM_F64: return kernel_times_t<P64, 2>(c, sign, in, reps, ms, st);
+            case TM_F32: return kernel_times_t<P32, 2>(c, sign, in, reps, ms, st);
+            case TM_BF16: return kernel_times_t<PB16, 2>(c, sign, in, reps, ms, st);
+            default: return kernel_times_t<PF16, 2>(c, sign, in, reps, ms, st);
+        }
+    }
+    switch (prec) {
+        case TM_F64: return kernel_times_t<P64, 1>(c, sign, in, reps, ms, st);
+        case TM_F32: return kernel_times_t<P32, 1>(c, sign, in, reps, ms, st);
+        case TM_BF16: return kernel_times_t<PB16, 1>(c, sign, in, reps, ms, st);
+        default: return kernel_times_t<PF16, 1>(c, sign, in, reps, ms, st);
+    }
 }
 
 // ---------------------------------------------------------------------------

@@ -76,6 +76,7 @@ _sigs = {
     "tm_solve_batch": [ct.POINTER(_vp), ct.c_int, ct.c_int, ct.POINTER(tm_solve_params), ct.POINTER(_vp),
                        ct.POINTER(_vp), ct.POINTER(tm_solve_info), _vp],
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
+    "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
 }
 for _n, _a in _sigs.items():
     getattr(lib, _n).argtypes = _a
@@ -211,3 +212,9 @@ def tm_power_iteration(ctx, op, iters=100, stream=None):
     v = ct.c_double()
     _check(lib.tm_power_iteration(ctx, int(op), int(iters), ct.byref(v), _stream(stream)))
     return v.value
+
+
+def tm_kernel_times(ctx, op, prec, inp, reps=20, stream=None):
+    ms = (ct.c_double * 2)()
+    _check(lib.tm_kernel_times(ctx, int(op), int(prec), ptr(inp), int(reps), ms, _stream(stream)))
+    return ms[0], ms[1]

@@ -13,7 +13,7 @@ these seeded fields stand in for them):
              (tr lambda_a lambda_b = 2 delta_ab); eps = EPS_PLAQ_059 gives a mean
              plaquette of 0.590 for uncorrelated links.
 * spinors    complex Gaussian, real and imaginary parts ~ N(0,1) i.i.d.
-* generator  numpy's Philox counter-based bit generator keyed by the seed.
+* generator  numpy's Philox counter-based bit generator, keyed by (seed, chunk).
 
 Canonical host layouts (C order, complex128):
   gauge        [t][z][y][x][mu][3][3]            mu = 0:x 1:y 2:z 3:t
@@ -22,6 +22,8 @@ Canonical host layouts (C order, complex128):
   heavy spinor [site_o][flavour 2][spin 4][colour 3]
 """
 from __future__ import annotations
+
+import os
 
 import numpy as np
 
@@ -87,17 +89,35 @@ def random_su3(n: int, eps: float, gen: np.random.Generator) -> np.ndarray:
     return reunitarise(_expm_i(eps * H))
 
 
-def gauge_field(dims, seed: int, eps: float = EPS_PLAQ_059) -> np.ndarray:
-    """Canonical gauge field [t][z][y][x][mu][3][3] complex128.  dims = (X,Y,Z,T)."""
+_LINK_CHUNK = 1 << 18
+
+
+def _link_chunk(args):
+    """Links [c*_LINK_CHUNK, c*_LINK_CHUNK + n) from the generator keyed (seed, c)."""
+    seed, c, n, eps = args
+    gen = np.random.Generator(np.random.Philox(key=(int(seed) << 32) | int(c)))
+    return random_su3(n, eps, gen)
+
+
+def gauge_field(dims, seed: int, eps: float = EPS_PLAQ_059, workers: int | None = None) -> np.ndarray:
+    """Canonical gauge field [t][z][y][x][mu][3][3] complex128.  dims = (X,Y,Z,T).
+
+    Links are made in chunks of 2^18, chunk c from its own Philox stream keyed
+    (seed, c), so the field does not depend on how many processes make it.
+    Large fields use a spawn-context process pool (safe after CUDA is up)."""
     X, Y, Z, T = dims
-    gen = rng(seed)
-    V = X * Y * Z * T
-    out = np.empty((V * 4, 3, 3), dtype=np.complex128)
-    chunk = 1 << 20
-    for s in range(0, V * 4, chunk):
-        e = min(V * 4, s + chunk)
-        out[s:e] = random_su3(e - s, eps, gen)
-    return out.reshape(T, Z, Y, X, 4, 3, 3)
+    n = X * Y * Z * T * 4
+    tasks = [(seed, c, min(_LINK_CHUNK, n - c * _LINK_CHUNK), eps)
+             for c in range((n + _LINK_CHUNK - 1) // _LINK_CHUNK)]
+    if workers is None:
+        workers = min(len(tasks), os.cpu_count() or 1, 32)
+    if workers > 1 and len(tasks) >= 8:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            parts = pool.map(_link_chunk, tasks, chunksize=1)
+    else:
+        parts = [_link_chunk(t) for t in tasks]
+    return np.concatenate(parts).reshape(T, Z, Y, X, 4, 3, 3)
 
 
 def unit_gauge(dims) -> np.ndarray:

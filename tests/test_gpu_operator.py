@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dirac as D
 from synth import fields as F
-from tests.gpu_util import PREC_TOL, Lat, rel
+from tests.gpu_util import PREC_TOL, Lat, rel, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -44,10 +44,10 @@ def test_light_schur_operators(setup, prec):
     dims, op, lat = setup
     tm = lat.tm
     psi = F.odd_spinor(dims, 7)
-    for code, ref in ((tm.TM_QHAT_PLUS, op.Qhat(psi, +1)), (tm.TM_QHAT_MINUS, op.Qhat(psi, -1)),
-                      (tm.TM_MDAGM, op.MdagM(psi)), (tm.TM_QPQM, op.QpQm(psi))):
+    for code, ref, n in ((tm.TM_QHAT_PLUS, op.Qhat(psi, +1), 1), (tm.TM_QHAT_MINUS, op.Qhat(psi, -1), 1),
+                         (tm.TM_MDAGM, op.MdagM(psi), 2), (tm.TM_QPQM, op.QpQm(psi), 2)):
         got = lat.apply(code, prec, psi)
-        assert rel(got, ref) < PREC_TOL[prec], (code, rel(got, ref))
+        assert rel(got, ref) < tol(prec, n), (code, rel(got, ref))
 
 
 @pytest.mark.parametrize("prec", [0, 1, 3, 2], ids=["f64", "f32", "f16", "bf16"])
@@ -55,10 +55,10 @@ def test_heavy_schur_operators(setup, prec):
     dims, op, lat = setup
     tm = lat.tm
     psi = F.odd_spinor(dims, 8, 2)
-    for code, ref in ((tm.TM_QH, op.Qhat_heavy(psi, +1)), (tm.TM_QH_DAG, op.Qhat_heavy(psi, -1)),
-                      (tm.TM_QH_SQ, op.heavy_sq(psi))):
+    for code, ref, n in ((tm.TM_QH, op.Qhat_heavy(psi, +1), 1), (tm.TM_QH_DAG, op.Qhat_heavy(psi, -1), 1),
+                         (tm.TM_QH_SQ, op.heavy_sq(psi), 2)):
         got = lat.apply(code, prec, psi)
-        assert rel(got, ref) < PREC_TOL[prec], (code, rel(got, ref))
+        assert rel(got, ref) < tol(prec, n), (code, rel(got, ref))
 
 
 def test_periodic_time_boundary():
