@@ -1,0 +1,348 @@
+#!/usr/bin/env python
+"""Benchmark of the even-odd twisted-mass clover solver path on GB300.
+
+Workload: light doublet on a 32^3x64 lattice (kappa 0.1400, csw 1.69, mu 0.0015,
+antiperiodic time), seeded synthetic SU(3) links (mean plaquette 0.59) and a
+complex-Gaussian right-hand side.
+
+One step = one application of the normal operator M_hat^dag M_hat = Q_hat_- Q_hat_+
+(two Schur operator applications, four kernels) in the mixed solver's storage
+format (FP16 fields with one FP32 scale per site, FP32 arithmetic).  The value is
+M_hat HBM GB/s: algorithmic bytes of the M_hat applications / device time.  The
+same JSON line carries the second half of the metric: seconds to true relative
+residual 1e-10 of the chosen form (mixed-precision CG) and of plain FP64 CG on
+the same GPU.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import configs as CFG  # noqa: E402
+from synth import fields as F  # noqa: E402
+
+METRIC = "Mhat HBM GB/s (% peak); seconds to rel res 1e-10, chosen form vs plain FP64 CG"
+W = CFG.LIGHT_32
+CPU_SAMPLE_DIMS = (16, 16, 16, 32)
+ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
+
+
+def mhat_bytes_per_site(prec):
+    """Algorithmic bytes of one M_hat application per odd site (each field read or
+    written once per pass): even pass links 8x18 + psi 24 + inverse blocks 144 +
+    t_e 24 reals, odd pass links 144 + t_e 24 + psi 24 + clover 72 + out 24 reals;
+    16-bit spinors add one FP32 scale per site per spinor access."""
+    esz = ESZ[prec]
+    scale = 4 if prec in (2, 3) else 0
+    k1 = 336 * esz + 2 * scale
+    k2 = 288 * esz + 3 * scale
+    return k1, k2
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) == 7:
+                self.rows.append(parts)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm = [float(r[0]) for r in self.rows if r[0].replace(".", "").isdigit()]
+        mx = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def traffic_from_profile(kernel_tag):
+    """DRAM bytes per launch recorded by ncu for the current kernel source, else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            rec = json.load(f)
+        src = open(os.path.join(ROOT, "paper_2212_06635_gb300", "csrc", "dslash.cu"), "rb").read()
+        entry = rec.get(kernel_tag)
+        if entry and entry.get("dslash_sha256") == hashlib.sha256(src).hexdigest():
+            return float(entry["dram_bytes_per_launch_full_size"])
+    except Exception:
+        pass
+    return None
+
+
+# ---------------------------------------------------------------------------
+def cpu_oracle_steps(nsteps, dims=CPU_SAMPLE_DIMS):
+    """Time the FP64 oracle applying M_hat^dag M_hat on a sub-lattice of the same
+    workload; returns (GB/s in FP64 algorithmic bytes, seconds per step)."""
+    from oracle import dirac as D
+    u = F.gauge_field(dims, W.link_seed)
+    op = D.TwistedMassClover(u, dims, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
+    op.inv_even_light(+1)
+    op.inv_even_light(-1)
+    b = F.odd_spinor(dims, W.rhs_seed)
+    vh = op.geo.V // 2
+    k1, k2 = mhat_bytes_per_site(0)
+    times = []
+    for _ in range(nsteps):
+        t0 = time.perf_counter()
+        op.MdagM(b)
+        times.append(time.perf_counter() - t0)
+    sec = float(np.mean(times))
+    return 2 * (k1 + k2) * vh / sec / 1e9, sec
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    nsteps = args.warmup + args.steps
+    t0 = time.perf_counter()
+    gbs, sec = cpu_oracle_steps(nsteps)
+    wall = time.perf_counter() - t0
+    sample = (f"oracle (numpy FP64, one thread) M_hat^dag M_hat on a {'x'.join(map(str, CPU_SAMPLE_DIMS))} "
+              f"sub-lattice of the same action, {nsteps} steps")
+    line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 2),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": W.name, "lattice": list(CPU_SAMPLE_DIMS),
+                                            "step": "M_hat^dag M_hat (2 M_hat), FP64 oracle"},
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": round(wall, 1)}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_2212_06635_gb300 import tm
+
+    dist = world > 1
+    if dist:
+        import torch.distributed as tdist
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    prec = {"f16": tm.TM_F16, "bf16": tm.TM_BF16, "f32": tm.TM_F32}[args.storage]
+
+    u = F.gauge_field(W.dims, W.link_seed)
+    b = F.odd_spinor(W.dims, W.rhs_seed)
+    vh = W.volume // 2
+    ctx = tm.tm_create(W.dims, local_rank)
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
+        bd = torch.from_numpy(b.view(np.float64).copy()).to(dev)
+        nbytes = tm.tm_field_bytes(ctx, prec, 1)
+        fin = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        fout = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        tm.tm_field_import(ctx, prec, 1, fin, bd)
+        torch.cuda.synchronize()
+        k1b, k2b = mhat_bytes_per_site(prec)
+        step_bytes = 2 * (k1b + k2b) * vh
+        stream = torch.cuda.current_stream()
+
+        def barrier():
+            if dist:
+                tdist.barrier()
+
+        # ---- device-resident steps -----------------------------------------
+        for _ in range(args.warmup):
+            tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, prec, fout, fin)
+        torch.cuda.synchronize()
+        clk = ClockSampler(torch.cuda.current_device() if not dist else local_rank)
+        clk.start()
+        barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, prec, fout, fin)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        clocks = clk.stop()
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            ms = float(t.item())
+        value = world * step_bytes * args.steps / (ms * 1e-3) / 1e9
+
+        # ---- dominant kernel against the roofline ------------------------------
+        t1, t2 = tm.tm_kernel_times(ctx, tm.TM_QHAT_PLUS, prec, fin, reps=50)
+        kernels = {"even pass (hop + inverse blocks)": (t1, k1b * vh), "odd pass (hop + clover + g5)": (t2, k2b * vh)}
+        dom = max(kernels, key=lambda k: kernels[k][0])
+        dms, dbytes = kernels[dom]
+        peak, peak_kind = peaks()
+        achieved = dbytes / (dms * 1e-3) / 1e9
+        tag = f"{'k1' if dom.startswith('even') else 'k2'}_{args.storage}"
+        traffic = traffic_from_profile(tag)
+
+        # ---- end to end through the C ABI with host buffers ---------------------
+        hin = torch.empty(vh * 24, dtype=torch.float64, pin_memory=True)
+        hin.copy_(torch.from_numpy(b.view(np.float64)))
+        hout = torch.empty_like(hin, pin_memory=True)
+        for _ in range(max(1, args.warmup // 2)):
+            tm.tm_field_import(ctx, prec, 1, fin, hin)
+            tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, prec, fout, fin)
+            tm.tm_field_export(ctx, prec, 1, hout, fout)
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            tm.tm_field_import(ctx, prec, 1, fin, hin)
+            tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, prec, fout, fin)
+            tm.tm_field_export(ctx, prec, 1, hout, fout)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        if dist:
+            t = torch.tensor([e2e_s], device=dev)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = world * step_bytes * args.steps / e2e_s / 1e9
+
+        # ---- seconds to true rel res 1e-10: chosen form vs FP64 CG ----------------
+        tts = {}
+        if not args.no_solve:
+            forms = [("chosen", prec, "mixed-precision CG: %s storage, FP32 math, FP64 reliable updates"
+                      % args.storage)]
+            if not args.no_fp64:
+                forms.append(("fp64_cg", tm.TM_F64, "plain FP64 CG"))
+            for name, sl, desc in forms:
+                x = torch.zeros_like(bd)
+                sp = tm.solve_params(tol=W.tol, sloppy=sl, maxiter=args.maxiter)
+                torch.cuda.synchronize()
+                info = tm.tm_solve_cg(ctx, tm.TM_MDAGM, sp, x, bd, check=False)
+                tts[name] = {"form": desc, "seconds": round(info.seconds, 4), "iters": info.iters,
+                             "reliable_updates": info.reliable_updates, "true_rel_res": info.true_rel_res,
+                             "status": tm.STATUS_NAMES[info.status]}
+            if "fp64_cg" in tts and tts["chosen"]["seconds"] > 0:
+                tts["speedup_vs_fp64_cg"] = round(tts["fp64_cg"]["seconds"] / tts["chosen"]["seconds"], 3)
+    finally:
+        tm.tm_destroy(ctx)
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        gbs, sec = cpu_oracle_steps(3)
+        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"FP64 numpy oracle, M_hat^dag M_hat on a {'x'.join(map(str, CPU_SAMPLE_DIMS))} "
+                         f"sub-lattice of the same action, 3 steps of {sec:.2f} s, host cores of this box"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": W.name, "lattice": list(W.dims), "kappa": W.kappa, "csw": W.csw, "mu": W.mu,
+                       "storage": args.storage, "math": "f32",
+                       "step": "M_hat^dag M_hat = Q_hat_- Q_hat_+ (2 M_hat, 4 kernels)",
+                       "bytes_per_step": step_bytes,
+                       "l2": "inputs larger than L2 (%.2f GB per step vs 0.13 GB L2)" % (step_bytes / 1e9),
+                       "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
+            "frac_of_peak": round(value / peak, 4),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
+                         "kernel_ms": round(dms, 5), "peak_kind": peak_kind},
+            "time_to_solution": tts,
+            "cpu_baseline": cpu,
+            "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": vh * 24 * 8,
+                    "d2h_bytes_per_step": vh * 24 * 8},
+            "gpu_launches": 4 * args.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--maxiter", type=int, default=60000)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG time-to-solution leg")
+    ap.add_argument("--no-solve", action="store_true", help="skip both time-to-solution legs")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl")
+    try:
+        return run_ours(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as tdist
+            tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    sys.exit(main())

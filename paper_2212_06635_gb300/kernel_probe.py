@@ -1,0 +1,64 @@
+"""Run the two passes of one Schur operator a few times on a seeded lattice, for
+profiling one kernel in isolation (e.g. under ncu with -k/-s/-c).
+
+  python -m paper_2212_06635_gb300.kernel_probe --dims 32 32 32 32 --prec f16 --reps 3
+
+Launch order: even pass x (1 + reps), then odd pass x reps (tm_kernel_times).
+Prints the CUDA-event time per launch of each pass and its algorithmic GB/s.
+"""
+from __future__ import annotations
+
+import argparse
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+PRECS = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
+ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
+    ap.add_argument("--prec", default="f16", choices=list(PRECS))
+    ap.add_argument("--heavy", action="store_true")
+    ap.add_argument("--reps", type=int, default=3)
+    a = ap.parse_args()
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    dims = tuple(a.dims)
+    prec = PRECS[a.prec]
+    nf = 2 if a.heavy else 1
+    u = F.gauge_field(dims, 1001)
+    b = F.odd_spinor(dims, 2001, nf)
+    ctx = tm.tm_create(dims, 0)
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, 0.14, 1.69, mu=0.0015, mubar=0.1246 if a.heavy else 0.0,
+                             epsbar=0.135 if a.heavy else 0.0)
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        f = torch.empty(tm.tm_field_bytes(ctx, prec, nf), dtype=torch.uint8, device="cuda")
+        tm.tm_field_import(ctx, prec, nf, f, bd)
+        op = tm.TM_QH if a.heavy else tm.TM_QHAT_PLUS
+        t1, t2 = tm.tm_kernel_times(ctx, op, prec, f, a.reps)
+        vh = int(np.prod(dims)) // 2
+        esz = ESZ[prec]
+        sc = 4 if prec >= 2 else 0
+        r1, r2 = (384, 360) if a.heavy else (336, 288)
+        s1, s2 = (2, 3)
+        b1 = (r1 * esz + s1 * sc) * vh
+        b2 = (r2 * esz + s2 * sc) * vh
+        print(f"dims {dims} prec {a.prec} nf {nf}: even pass {t1 * 1e3:.1f} us {b1 / t1 / 1e6:.0f} GB/s; "
+              f"odd pass {t2 * 1e3:.1f} us {b2 / t2 / 1e6:.0f} GB/s")
+    finally:
+        tm.tm_destroy(ctx)
+
+
+if __name__ == "__main__":
+    main()
