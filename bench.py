@@ -239,7 +239,7 @@ def run_ours(args, rank, world, local_rank):
 
         # ---- end to end through the C ABI with host buffers ---------------------
         hin = torch.empty(vh * 24, dtype=torch.float64, pin_memory=True)
-        hin.copy_(torch.from_numpy(b.view(np.float64)))
+        hin.copy_(torch.from_numpy(b.view(np.float64).reshape(-1)))
         hout = torch.empty_like(hin, pin_memory=True)
         for _ in range(max(1, args.warmup // 2)):
             tm.tm_field_import(ctx, prec, 1, fin, hin)

@@ -130,6 +130,13 @@ tm_status tm_field_import(tm_ctx* ctx, tm_prec prec, int nflavour, void* dst_nat
 tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_canonical,
                           const void* src_native, void* stream);
 
+/* *result (device pointer, FP64) = ||field||^2 of a native field: per-thread sums
+ * in the arithmetic precision, FP64 across threads and blocks, block partials
+ * summed in a fixed order by the last block (deterministic for a given size).
+ * Stream-ordered; uses the context's reduction scratch. */
+tm_status tm_field_norm2(tm_ctx* ctx, tm_prec prec, int nflavour, const void* field, double* result,
+                         void* stream);
+
 /* out = op(in), native fields of precision prec on the device (eq:hQpm / eq:hQh).
  * Light ops take nflavour-1 fields, heavy ops nflavour-2 fields.  out != in.
  * Returns TM_ERR_STALE if the clover term predates the gauge field. */

@@ -528,6 +528,31 @@ static VecBatch<1> vb1(const tm_ctx* c, void* v0, void* v1 = nullptr, void* v2 =
     return b;
 }
 
+template <int P>
+static cudaError_t norm2_t(tm_ctx* c, int nf, const void* f, double* res, cudaStream_t st) {
+    VecBatch<1> b = vb1(c, const_cast<void*>(f), nullptr, nullptr, nullptr, res);
+    return nf == 1 ? launch_norm2<P, 12, 1>(b, nblk(c->vh, BLAS_BS), st)
+                   : launch_norm2<P, 24, 1>(b, nblk(c->vh, BLAS_BS), st);
+}
+
+extern "C" tm_status tm_field_norm2(tm_ctx* c, tm_prec prec, int nf, const void* field, double* result,
+                                    void* stream) {
+    if (!c || !field || !result || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_norm2: bad argument");
+    if (((uintptr_t)field & 15) || ((uintptr_t)result & 7))
+        return fail(TM_ERR_ARG, "tm_field_norm2: misaligned pointer");
+    CKS(check_prec(prec));
+    if (!is_device_ptr(result)) return fail(TM_ERR_ARG, "tm_field_norm2: result must be a device pointer");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    switch (prec) {
+        case TM_F64: CK(norm2_t<P64>(c, nf, field, result, st)); break;
+        case TM_F32: CK(norm2_t<P32>(c, nf, field, result, st)); break;
+        case TM_BF16: CK(norm2_t<PB16>(c, nf, field, result, st)); break;
+        default: CK(norm2_t<PF16>(c, nf, field, result, st)); break;
+    }
+    return TM_OK;
+}
+
 static tm_status read_scalar(tm_ctx* c, double* dev, double* out, cudaStream_t st) {
     CK(cudaMemcpyAsync(c->h_scal, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
@@ -616,6 +641,11 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
     CKS((norm2_dev<P64, NC>(c, b64, st, &bb)));
     info->iters = 0;
     info->reliable_updates = 0;
+    if (!std::isfinite(bb)) {
+        info->true_rel_res = bb;
+        info->status = TM_ERR_BREAKDOWN;
+        return fail(TM_ERR_BREAKDOWN, "solve: right-hand side is not finite");
+    }
     if (!(bb > 0)) {
         CK(cudaMemsetAsync(x64, 0, b64sz, st));
         info->true_rel_res = 0.0;
@@ -806,6 +836,9 @@ static tm_status multishift_core(tm_ctx* c, tm_op op, int ns, const double* sh_s
     const int nb = nblk(vh, BLAS_BS);
     double bb;
     CKS((norm2_dev<P64, NC>(c, b64, st, &bb)));
+    if (!std::isfinite(bb) || !(bb > 0))
+        return fail(std::isfinite(bb) ? TM_ERR_ARG : TM_ERR_BREAKDOWN,
+                    "multishift: right-hand side must be finite and non-zero");
     CK((launch_convert<PS, P64, NC, 1>(vb1(c, rs, b64), nb, st)));
     // the sloppy multishift stops each shift near the precision floor of PS
     const double floor_tol = PS == P64 ? 0.0 : (PS == P32 ? 1e-6 : 2e-4);
@@ -1030,6 +1063,7 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
         CKS(ws_get(c, WS_MID64, sz, &mid64));
         CKS((norm2_dev<P64, NC>(c, w[q].b64, st, &bb[q])));
         infos[q] = tm_solve_info{};
+        if (!std::isfinite(bb[q])) { infos[q].status = TM_ERR_BREAKDOWN; done[q] = 1; continue; }
         if (!(bb[q] > 0)) { CK(cudaMemsetAsync(w[q].x64, 0, sz, st)); done[q] = 1; continue; }
         CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
         if (rr[q] <= tol * tol * bb[q]) { done[q] = 1; continue; }

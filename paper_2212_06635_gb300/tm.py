@@ -77,6 +77,7 @@ _sigs = {
                        ct.POINTER(_vp), ct.POINTER(tm_solve_info), _vp],
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
+    "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
 }
 for _n, _a in _sigs.items():
     getattr(lib, _n).argtypes = _a
@@ -167,6 +168,11 @@ def tm_field_import(ctx, prec, nflavour, dst, src, stream=None):
 
 def tm_field_export(ctx, prec, nflavour, dst, src, stream=None):
     _check(lib.tm_field_export(ctx, int(prec), int(nflavour), ptr(dst), ptr(src), _stream(stream)))
+
+
+def tm_field_norm2(ctx, prec, nflavour, field, result, stream=None):
+    """result: device tensor with at least one float64 element."""
+    _check(lib.tm_field_norm2(ctx, int(prec), int(nflavour), ptr(field), ptr(result), _stream(stream)))
 
 
 def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
