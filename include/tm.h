@@ -176,6 +176,24 @@ tm_status tm_power_iteration(tm_ctx* ctx, tm_op op, int iters, double* lambda_ma
 tm_status tm_kernel_times(tm_ctx* ctx, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
                           void* stream);
 
+/* Stencil kernel variant of each pass of the Schur operator for one storage
+ * precision and flavour count: 0 = direct (operands loaded into registers),
+ * 1 = shared-memory staged (asynchronous copies of the neighbour spinors, links
+ * and site-local blocks, two directions ahead; FP32 and 16-bit only). */
+typedef struct {
+    int even_pass;   /* hop + inverse blocks   */
+    int odd_pass;    /* hop + clover + g5      */
+} tm_tuning;
+
+/* Autotuner: time both variants of both passes on this context's lattice and
+ * keep the faster of each (used by every later operator, solver and batch
+ * call).  If the environment variable TM_TUNE_CACHE names a file, choices are
+ * read from / appended to it, keyed by "X Y Z T prec nflavour".  FP64 always
+ * uses the direct kernel.  `chosen` may be NULL. */
+tm_status tm_autotune(tm_ctx* ctx, tm_prec prec, int nflavour, tm_tuning* chosen, void* stream);
+tm_status tm_set_tuning(tm_ctx* ctx, tm_prec prec, int nflavour, const tm_tuning* tuning);
+tm_status tm_get_tuning(const tm_ctx* ctx, tm_prec prec, int nflavour, tm_tuning* tuning);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* tm_last_error(void);
 

@@ -89,7 +89,7 @@ static tm_status ws_get(tm_ctx* c, int id, size_t bytes, void** out) {
 enum WsId {
     WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
-    WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO,
+    WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO, WS_TUNE,
     WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
 };
 
@@ -106,7 +106,7 @@ extern "C" tm_status tm_create(tm_ctx** out, const int dims[4], int device) {
     c->g.X = dims[0]; c->g.Y = dims[1]; c->g.Z = dims[2]; c->g.T = dims[3];
     c->vh = (long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
     c->g.vh = c->vh;
-    c->max_blocks = std::max(nblk(c->vh, DSLASH_BS), nblk(c->vh, BLAS_BS));
+    c->max_blocks = nblk(c->vh, MIN_BS);
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking);
     e = e ? e : cudaMalloc(&c->partial, sizeof(double) * c->max_blocks);
@@ -272,11 +272,25 @@ static const void* clovH_ptr(const tm_ctx* c, int P) { return P == P64 ? (const 
 // ---------------------------------------------------------------------------
 // operator application
 // ---------------------------------------------------------------------------
+// block size of a stencil pass in the context's chosen variant
+static int pass_bs(const tm_ctx* c, int P, int nf, int kind) {
+    return c->variant[P][nf - 1][kind] ? STAGED_BS : DSLASH_BS;
+}
+
+// launch one pass in the variant the context chose for (P, NF, KIND)
+template <int P, int NF, int KIND, int NP>
+static cudaError_t launch_pass(int variant, const OpBatch<NP>& b, int nb, cudaStream_t st) {
+    if constexpr (P != P64) {
+        if (variant) return launch_dslash_staged<P, NF, KIND, NP>(b, nb, st);
+    }
+    return launch_dslash<P, NF, KIND, NP>(b, nb, st);
+}
+
 static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void* out, const void* in,
                         const void* loc, SolverCtl* ctl, bool fuse) {
     OpProb p{};
     p.g = c->g;
-    p.nblk = nblk(c->vh, DSLASH_BS);
+    p.nblk = nblk(c->vh, pass_bs(c, P, nf, kind));
     p.bc_t = (float)c->params.bc_t;
     p.gauge[0] = gauge_ptr(c, P, 0);
     p.gauge[1] = gauge_ptr(c, P, 1);
@@ -303,15 +317,15 @@ static cudaError_t schur(const tm_ctx* c, int sign, void* out, const void* in, v
     OpBatch<1> b{};
     b.n = 1;
     b.fin = FIN_NONE;
-    const int nb = nblk(c->vh, DSLASH_BS);
-    b.blk_start[0] = 0;
-    b.blk_start[1] = nb;
     b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, ctl, false);
-    cudaError_t e = launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st);
+    b.blk_start[0] = 0;
+    b.blk_start[1] = b.p[0].nblk;
+    cudaError_t e = launch_pass<P, NF, K1_EO_INV, 1>(c->variant[P][NF - 1][K1_EO_INV], b, b.p[0].nblk, st);
     if (e != cudaSuccess) return e;
     b.fin = fin;
     b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, ctl, fin != FIN_NONE);
-    return launch_dslash<P, NF, K2_OE_LOCAL, 1>(b, nb, st);
+    b.blk_start[1] = b.p[0].nblk;
+    return launch_pass<P, NF, K2_OE_LOCAL, 1>(c->variant[P][NF - 1][K2_OE_LOCAL], b, b.p[0].nblk, st);
 }
 
 // signs of the two factors of a normal operator (first applied first)
@@ -447,27 +461,30 @@ extern "C" tm_status tm_field_export(tm_ctx* c, tm_prec prec, int nf, double* ds
 }
 
 template <int P, int NF>
-static tm_status kernel_times_t(tm_ctx* c, int sign, const void* in, int reps, double* ms, cudaStream_t st) {
+static tm_status kernel_times_t(tm_ctx* c, int sign, const void* in, int reps, double* ms, cudaStream_t st,
+                                int v1, int v2) {
     void *te = nullptr, *out = nullptr;
     CKS(ws_get(c, WS_APPLY_TE, spinor_bytes(P, 12 * NF, c->vh), &te));
     CKS(ws_get(c, WS_APPLY_MID, spinor_bytes(P, 12 * NF, c->vh), &out));
     OpBatch<1> b{};
     b.n = 1;
     b.fin = FIN_NONE;
-    const int nb = nblk(c->vh, DSLASH_BS);
     b.blk_start[0] = 0;
-    b.blk_start[1] = nb;
     cudaEvent_t e0, e1, e2;
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
     CK(cudaEventCreate(&e2));
     b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, nullptr, false);
-    CK((launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st)));   // warm-up
+    int nb = b.p[0].nblk = nblk(c->vh, v1 ? STAGED_BS : DSLASH_BS);
+    b.blk_start[1] = nb;
+    CK((launch_pass<P, NF, K1_EO_INV, 1>(v1, b, nb, st)));   // warm-up
     CK(cudaEventRecord(e0, st));
-    for (int r = 0; r < reps; ++r) CK((launch_dslash<P, NF, K1_EO_INV, 1>(b, nb, st)));
+    for (int r = 0; r < reps; ++r) CK((launch_pass<P, NF, K1_EO_INV, 1>(v1, b, nb, st)));
     CK(cudaEventRecord(e1, st));
     b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, nullptr, false);
-    for (int r = 0; r < reps; ++r) CK((launch_dslash<P, NF, K2_OE_LOCAL, 1>(b, nb, st)));
+    nb = b.p[0].nblk = nblk(c->vh, v2 ? STAGED_BS : DSLASH_BS);
+    b.blk_start[1] = nb;
+    for (int r = 0; r < reps; ++r) CK((launch_pass<P, NF, K2_OE_LOCAL, 1>(v2, b, nb, st)));
     CK(cudaEventRecord(e2, st));
     CK(cudaEventSynchronize(e2));
     float t1 = 0, t2 = 0;
@@ -477,6 +494,24 @@ static tm_status kernel_times_t(tm_ctx* c, int sign, const void* in, int reps, d
     ms[1] = t2 / reps;
     cudaEventDestroy(e0); cudaEventDestroy(e1); cudaEventDestroy(e2);
     return TM_OK;
+}
+
+static tm_status kernel_times_any(tm_ctx* c, int prec, int nf, int sign, const void* in, int reps, double* ms,
+                                  cudaStream_t st, int v1, int v2) {
+    if (nf == 2) {
+        switch (prec) {
+            case TM_F64: return kernel_times_t<P64, 2>(c, sign, in, reps, ms, st, 0, 0);
+            case TM_F32: return kernel_times_t<P32, 2>(c, sign, in, reps, ms, st, v1, v2);
+            case TM_BF16: return kernel_times_t<PB16, 2>(c, sign, in, reps, ms, st, v1, v2);
+            default: return kernel_times_t<PF16, 2>(c, sign, in, reps, ms, st, v1, v2);
+        }
+    }
+    switch (prec) {
+        case TM_F64: return kernel_times_t<P64, 1>(c, sign, in, reps, ms, st, 0, 0);
+        case TM_F32: return kernel_times_t<P32, 1>(c, sign, in, reps, ms, st, v1, v2);
+        case TM_BF16: return kernel_times_t<PB16, 1>(c, sign, in, reps, ms, st, v1, v2);
+        default: return kernel_times_t<PF16, 1>(c, sign, in, reps, ms, st, v1, v2);
+    }
 }
 
 extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
@@ -489,21 +524,99 @@ extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const vo
     const cudaStream_t st = S(stream);
     CKS(ensure_prec(c, prec, st));
     const int sign = (op == TM_QHAT_PLUS || op == TM_QH) ? +1 : -1;
-    if (nflav(op) == 2) {
-        if (!c->have_heavy) return fail(TM_ERR_ARG, "tm_kernel_times: no heavy clover term");
-        switch (prec) {
-            case TM_F64: return kernel_times_t<P64, 2>(c, sign, in, reps, ms, st);
-            case TM_F32: return kernel_times_t<P32, 2>(c, sign, in, reps, ms, st);
-            case TM_BF16: return kernel_times_t<PB16, 2>(c, sign, in, reps, ms, st);
-            default: return kernel_times_t<PF16, 2>(c, sign, in, reps, ms, st);
+    const int nf = nflav(op);
+    if (nf == 2 && !c->have_heavy) return fail(TM_ERR_ARG, "tm_kernel_times: no heavy clover term");
+    return kernel_times_any(c, prec, nf, sign, in, reps, ms, st, c->variant[prec][nf - 1][0],
+                            c->variant[prec][nf - 1][1]);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: per (lattice, precision, flavours) pick the faster stencil variant
+// of each pass by timing both on this context's own fields; results are kept in
+// the context and, if TM_TUNE_CACHE names a file, in a text cache keyed by
+// "X Y Z T prec nflavour" so later processes skip the timing.
+// ---------------------------------------------------------------------------
+static bool tune_cache_lookup(const tm_ctx* c, int prec, int nf, tm_tuning* t) {
+    const char* path = getenv("TM_TUNE_CACHE");
+    if (!path || !*path) return false;
+    FILE* f = fopen(path, "r");
+    if (!f) return false;
+    int X, Y, Z, T, p, n, a, b;
+    bool found = false;
+    while (fscanf(f, "%d %d %d %d %d %d %d %d", &X, &Y, &Z, &T, &p, &n, &a, &b) == 8) {
+        if (X == c->g.X && Y == c->g.Y && Z == c->g.Z && T == c->g.T && p == prec && n == nf) {
+            t->even_pass = a;
+            t->odd_pass = b;
+            found = true;
         }
     }
-    switch (prec) {
-        case TM_F64: return kernel_times_t<P64, 1>(c, sign, in, reps, ms, st);
-        case TM_F32: return kernel_times_t<P32, 1>(c, sign, in, reps, ms, st);
-        case TM_BF16: return kernel_times_t<PB16, 1>(c, sign, in, reps, ms, st);
-        default: return kernel_times_t<PF16, 1>(c, sign, in, reps, ms, st);
+    fclose(f);
+    return found;
+}
+
+static void tune_cache_store(const tm_ctx* c, int prec, int nf, const tm_tuning* t) {
+    const char* path = getenv("TM_TUNE_CACHE");
+    if (!path || !*path) return;
+    FILE* f = fopen(path, "a");
+    if (!f) return;
+    fprintf(f, "%d %d %d %d %d %d %d %d\n", c->g.X, c->g.Y, c->g.Z, c->g.T, prec, nf, t->even_pass, t->odd_pass);
+    fclose(f);
+}
+
+static tm_status check_tuning(int prec, int nf, const tm_tuning* t) {
+    if (nf != 1 && nf != 2) return fail(TM_ERR_ARG, "tuning: nflavour must be 1 or 2");
+    if ((t->even_pass != 0 && t->even_pass != 1) || (t->odd_pass != 0 && t->odd_pass != 1))
+        return fail(TM_ERR_ARG, "tuning: variants are 0 (direct) or 1 (staged)");
+    if (prec == TM_F64 && (t->even_pass || t->odd_pass))
+        return fail(TM_ERR_UNSUPPORTED, "tuning: the staged variant has no FP64 form");
+    return TM_OK;
+}
+
+extern "C" tm_status tm_set_tuning(tm_ctx* c, tm_prec prec, int nf, const tm_tuning* t) {
+    if (!c || !t) return fail(TM_ERR_ARG, "tm_set_tuning: null argument");
+    CKS(check_prec(prec));
+    CKS(check_tuning(prec, nf, t));
+    c->variant[prec][nf - 1][0] = t->even_pass;
+    c->variant[prec][nf - 1][1] = t->odd_pass;
+    return TM_OK;
+}
+
+extern "C" tm_status tm_get_tuning(const tm_ctx* c, tm_prec prec, int nf, tm_tuning* t) {
+    if (!c || !t || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_get_tuning: bad argument");
+    CKS(check_prec(prec));
+    t->even_pass = c->variant[prec][nf - 1][0];
+    t->odd_pass = c->variant[prec][nf - 1][1];
+    return TM_OK;
+}
+
+extern "C" tm_status tm_autotune(tm_ctx* c, tm_prec prec, int nf, tm_tuning* chosen, void* stream) {
+    if (!c || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_autotune: bad argument");
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    tm_tuning t{0, 0};
+    if (prec != TM_F64 && !tune_cache_lookup(c, prec, nf, &t)) {
+        if (nf == 2 && !c->have_heavy) return fail(TM_ERR_ARG, "tm_autotune: no heavy clover term");
+        const cudaStream_t st = S(stream);
+        CKS(ensure_prec(c, prec, st));
+        void* f = nullptr;
+        CKS(ws_get(c, WS_TUNE, spinor_bytes(prec, 12 * nf, c->vh), &f));
+        void* canon = nullptr;
+        const size_t cb = sizeof(double) * 24 * nf * c->vh;
+        CKS(ws_get(c, WS_STAGE_IO, cb, &canon));
+        CK(cudaMemsetAsync(canon, 0, cb, st));
+        CK(import_any(prec, nf, f, reinterpret_cast<const double*>(canon), c->vh, st));
+        double direct[2], staged[2];
+        const int reps = c->vh >= (1 << 18) ? 5 : 20;
+        CKS(kernel_times_any(c, prec, nf, +1, f, reps, direct, st, 0, 0));
+        CKS(kernel_times_any(c, prec, nf, +1, f, reps, staged, st, 1, 1));
+        t.even_pass = staged[0] < direct[0] ? 1 : 0;
+        t.odd_pass = staged[1] < direct[1] ? 1 : 0;
+        tune_cache_store(c, prec, nf, &t);
     }
+    c->variant[prec][nf - 1][0] = t.even_pass;
+    c->variant[prec][nf - 1][1] = t.odd_pass;
+    if (chosen) *chosen = t;
+    return TM_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -1086,17 +1199,23 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
     VecBatch<MAXP> pu{}, up{};
     int s1, s2;
     normal_signs(op, &s1, &s2);
-    int ob = 0, vbk = 0;
+    // one kernel variant per pass for the whole batch (the first context's choice)
+    const int v1 = cs[0]->variant[PS][0][K1_EO_INV], v2 = cs[0]->variant[PS][0][K2_OE_LOCAL];
+    int ob1 = 0, ob2 = 0, vbk = 0;
     for (int q = 0; q < n; ++q) {
         tm_ctx* c = cs[q];
-        const int nbd = nblk(c->vh, DSLASH_BS), nbb = nblk(c->vh, BLAS_BS);
+        const int nb1 = nblk(c->vh, v1 ? STAGED_BS : DSLASH_BS), nb2 = nblk(c->vh, v2 ? STAGED_BS : DSLASH_BS);
+        const int nbb = nblk(c->vh, BLAS_BS);
         SolverCtl* ctl = c->ctl;
-        k1.blk_start[q] = k2a.blk_start[q] = k1b.blk_start[q] = k2b.blk_start[q] = ob;
+        k1.blk_start[q] = k1b.blk_start[q] = ob1;
+        k2a.blk_start[q] = k2b.blk_start[q] = ob2;
         pu.blk_start[q] = up.blk_start[q] = vbk;
         k1.p[q] = make_prob(c, PS, 1, K1_EO_INV, s1, w[q].tes, w[q].ps, nullptr, ctl, false);
         k2a.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s1, w[q].mids, w[q].tes, w[q].ps, ctl, true);
         k1b.p[q] = make_prob(c, PS, 1, K1_EO_INV, s2, w[q].tes, w[q].mids, nullptr, ctl, false);
         k2b.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s2, w[q].aps, w[q].tes, w[q].mids, ctl, false);
+        k1.p[q].nblk = k1b.p[q].nblk = nb1;
+        k2a.p[q].nblk = k2b.p[q].nblk = nb2;
         VecBatch<1> a = vb1(c, w[q].ps, w[q].rs);
         pu.p[q] = a.p[0];
         VecBatch<1> u = vb1(c, w[q].xs, w[q].ps, w[q].rs, w[q].aps);
@@ -1105,19 +1224,21 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
             c->h_ctl->flag = CTL_STOP;
             CKS(put_ctl(c, st));
         }
-        ob += nbd;
+        ob1 += nb1;
+        ob2 += nb2;
         vbk += nbb;
     }
-    for (auto* t : {&k1, &k2a, &k1b, &k2b}) { t->n = n; t->blk_start[n] = ob; t->fin = FIN_NONE; }
+    for (auto* t : {&k1, &k1b}) { t->n = n; t->blk_start[n] = ob1; t->fin = FIN_NONE; }
+    for (auto* t : {&k2a, &k2b}) { t->n = n; t->blk_start[n] = ob2; t->fin = FIN_NONE; }
     k2a.fin = FIN_CG_ALPHA;
     pu.n = up.n = n;
     pu.blk_start[n] = up.blk_start[n] = vbk;
     auto iteration = [&]() -> cudaError_t {
         cudaError_t e = launch_cg_pupdate<PS, NC, MAXP>(pu, vbk, st);
-        if (!e) e = launch_dslash<PS, 1, K1_EO_INV, MAXP>(k1, ob, st);
-        if (!e) e = launch_dslash<PS, 1, K2_OE_LOCAL, MAXP>(k2a, ob, st);
-        if (!e) e = launch_dslash<PS, 1, K1_EO_INV, MAXP>(k1b, ob, st);
-        if (!e) e = launch_dslash<PS, 1, K2_OE_LOCAL, MAXP>(k2b, ob, st);
+        if (!e) e = launch_pass<PS, 1, K1_EO_INV, MAXP>(v1, k1, ob1, st);
+        if (!e) e = launch_pass<PS, 1, K2_OE_LOCAL, MAXP>(v2, k2a, ob2, st);
+        if (!e) e = launch_pass<PS, 1, K1_EO_INV, MAXP>(v1, k1b, ob1, st);
+        if (!e) e = launch_pass<PS, 1, K2_OE_LOCAL, MAXP>(v2, k2b, ob2, st);
         if (!e) e = launch_cg_update<PS, PX, NC, MAXP>(up, vbk, st);
         return e;
     };

@@ -47,4 +47,8 @@ struct tm_ctx {
     double* h_scal = nullptr;
 
     std::map<int, std::pair<void*, size_t>> ws;   // workspace buffers by id
+
+    // stencil kernel variant per [storage precision][flavours - 1][pass]:
+    // 0 = direct (registers), 1 = shared-memory staged; set by tm_autotune / tm_set_tuning
+    int variant[4][2][2] = {};
 };

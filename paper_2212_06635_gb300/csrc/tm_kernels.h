@@ -7,8 +7,10 @@
 
 namespace tmk {
 
-constexpr int DSLASH_BS = 128;
+constexpr int DSLASH_BS = 128;   // direct stencil kernel
+constexpr int STAGED_BS = 64;    // shared-memory staged stencil kernel
 constexpr int BLAS_BS = 256;
+constexpr int MIN_BS = 64;       // smallest block size of any reducing kernel (sizes the partials)
 
 enum DslashKind { K1_EO_INV = 0, K2_OE_LOCAL = 1 };
 
@@ -166,6 +168,9 @@ struct MsVecs {
 // ---------------------------------------------------------------------------
 template <int P, int NF, int KIND, int NP>
 cudaError_t launch_dslash(const OpBatch<NP>& b, int nblocks, cudaStream_t st);
+// shared-memory staged variant (FP32 / 16-bit storage), STAGED_BS threads per block
+template <int P, int NF, int KIND, int NP>
+cudaError_t launch_dslash_staged(const OpBatch<NP>& b, int nblocks, cudaStream_t st);
 
 // p = r + beta p (+ ||p||^2 when the problem has a shift)       v = {p, r}
 template <int P, int NC, int NP>

@@ -45,6 +45,10 @@ class tm_solve_info(ct.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class tm_tuning(ct.Structure):
+    _fields_ = [("even_pass", ct.c_int), ("odd_pass", ct.c_int)]
+
+
 class TMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -78,6 +82,9 @@ _sigs = {
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_autotune": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning), _vp],
+    "tm_set_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
+    "tm_get_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
 }
 for _n, _a in _sigs.items():
     getattr(lib, _n).argtypes = _a
@@ -224,3 +231,20 @@ def tm_kernel_times(ctx, op, prec, inp, reps=20, stream=None):
     ms = (ct.c_double * 2)()
     _check(lib.tm_kernel_times(ctx, int(op), int(prec), ptr(inp), int(reps), ms, _stream(stream)))
     return ms[0], ms[1]
+
+
+def tm_autotune(ctx, prec, nflavour=1, stream=None):
+    t = tm_tuning()
+    _check(lib.tm_autotune(ctx, int(prec), int(nflavour), ct.byref(t), _stream(stream)))
+    return t.even_pass, t.odd_pass
+
+
+def tm_set_tuning(ctx, prec, nflavour, even_pass, odd_pass):
+    t = tm_tuning(int(even_pass), int(odd_pass))
+    _check(lib.tm_set_tuning(ctx, int(prec), int(nflavour), ct.byref(t)))
+
+
+def tm_get_tuning(ctx, prec, nflavour=1):
+    t = tm_tuning()
+    _check(lib.tm_get_tuning(ctx, int(prec), int(nflavour), ct.byref(t)))
+    return t.even_pass, t.odd_pass

@@ -90,3 +90,36 @@ def test_full_size_sampled_32x64():
             assert rel(got, ref) < PREC_TOL[prec], (prec, rel(got, ref))
     finally:
         lat.close()
+
+
+@pytest.mark.parametrize("prec", [1, 3, 2], ids=["f32", "f16", "bf16"])
+def test_staged_variant_matches_oracle(setup, prec):
+    """The shared-memory staged stencil kernels give the oracle's operator too
+    (light and heavy, both passes forced to the staged variant)."""
+    dims, op, lat = setup
+    tm = lat.tm
+    psi = F.odd_spinor(dims, 9)
+    psi2 = F.odd_spinor(dims, 10, 2)
+    for ev, od in ((1, 1), (1, 0), (0, 1)):
+        tm.tm_set_tuning(lat.ctx, prec, 1, ev, od)
+        tm.tm_set_tuning(lat.ctx, prec, 2, ev, od)
+        assert rel(lat.apply(tm.TM_QHAT_PLUS, prec, psi), op.Qhat(psi, +1)) < tol(prec)
+        assert rel(lat.apply(tm.TM_MDAGM, prec, psi), op.MdagM(psi)) < tol(prec, 2)
+        assert rel(lat.apply(tm.TM_QH_DAG, prec, psi2), op.Qhat_heavy(psi2, -1)) < tol(prec)
+    tm.tm_set_tuning(lat.ctx, prec, 1, 0, 0)
+    tm.tm_set_tuning(lat.ctx, prec, 2, 0, 0)
+
+
+def test_autotune_choice_is_kept():
+    dims = (8, 8, 4, 8)
+    u = F.gauge_field(dims, 61)
+    lat = Lat(u, dims, KAPPA, CSW, mu=MU)
+    try:
+        tm = lat.tm
+        choice = tm.tm_autotune(lat.ctx, tm.TM_F16, 1)
+        assert tm.tm_get_tuning(lat.ctx, tm.TM_F16, 1) == choice
+        assert tm.tm_autotune(lat.ctx, tm.TM_F64, 1) == (0, 0)
+        with pytest.raises(tm.TMError):
+            tm.tm_set_tuning(lat.ctx, tm.TM_F64, 1, 1, 1)
+    finally:
+        lat.close()

@@ -201,3 +201,29 @@ def test_maxiter_and_nan_and_stale():
         lat.apply(tm.TM_QHAT_PLUS, 0, b)
     finally:
         lat.close()
+
+
+def test_solvers_with_staged_kernels():
+    """Mixed CG, multishift and batch with the staged stencil variant."""
+    dims = (8, 8, 8, 8)
+    op, lat = _lat(dims, 1800, kappa=0.14, mu=0.004, mubar=0.1246, epsbar=0.135)
+    tm = lat.tm
+    try:
+        for prec in (tm.TM_F32, tm.TM_F16):
+            for nf in (1, 2):
+                tm.tm_set_tuning(lat.ctx, prec, nf, 1, 1)
+        b = F.odd_spinor(dims, 1801)
+        x = to_dev(np.zeros_like(b))
+        tm.tm_solve_cg(lat.ctx, tm.TM_MDAGM, tm.solve_params(tol=1e-10, sloppy=tm.TM_F16), x, to_dev(b))
+        assert S.rel_residual(op.MdagM, from_dev(x, b.shape), b) <= 1.05e-10
+        b2 = F.odd_spinor(dims, 1802, 2)
+        shifts = [1e-3, 0.1]
+        xs = [to_dev(np.zeros_like(b2)) for _ in shifts]
+        tm.tm_solve_multishift(lat.ctx, tm.TM_QH_SQ, shifts, xs, to_dev(b2), tm.solve_params(sloppy=tm.TM_F32))
+        for s, xx in zip(shifts, xs):
+            assert S.rel_residual(lambda v, s=s: op.heavy_sq(v) + s * v, from_dev(xx, b2.shape), b2) <= 1.05e-10
+        x.zero_()
+        tm.tm_solve_batch([lat.ctx], tm.TM_MDAGM, tm.solve_params(sloppy=tm.TM_F16), [x], [to_dev(b)])
+        assert S.rel_residual(op.MdagM, from_dev(x, b.shape), b) <= 1.05e-10
+    finally:
+        lat.close()
