@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "tm_host.h"
+#include "ptc.h"
 
 using namespace tmk;
 
@@ -90,6 +91,7 @@ enum WsId {
     WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
     WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO, WS_TUNE,
+    WS_FCG_Z, WS_FCG_PO, WS_FCG_QO,
     WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
 };
 
@@ -1370,4 +1372,459 @@ extern "C" tm_status tm_solve_batch(tm_ctx** cs, int n, tm_op op, const tm_solve
     for (int q = 0; q < n; ++q) infos[q].seconds = secs;
     if (s != TM_OK) fail(s, "tm_solve_batch: at least one problem failed");
     return s;
+}
+
+// ---------------------------------------------------------------------------
+// learned preconditioner: gauge-equivariant parallel-transport network
+// ---------------------------------------------------------------------------
+struct tm_ptc {
+    int device = 0;
+    int L = 0;
+    int ch[9] = {};
+    float2* W[8] = {};      // complex FP32 master weights [9][cout][cin][4][4]
+    float2* m[8] = {};      // Adam first and second moments
+    float2* v[8] = {};
+    float2* G[8] = {};      // gradient accumulators
+    void* wf[8] = {};       // BF16 real-embedded forward weights, 9 x 64 x 64
+    void* wa[8] = {};       // BF16 real-embedded adjoint weights
+    int step = 0;
+    long V = 0;             // geometry of the activation buffers
+    void* act[9] = {};      // activations per layer boundary, BF16 [ch][3][V] uint4
+    void* del[2] = {};      // back-propagated deltas (8 channels)
+    float* wpart = nullptr; // weight-gradient partials
+    int nchunk = 0;
+    double* dpart = nullptr;
+    double* dscal = nullptr;   // [0] ||e||^2, [1] loss sum, [2..] scratch
+    double* hscal = nullptr;
+    void* e32 = nullptr;       // training error vector (FP32 native odd)
+    void* r32 = nullptr;       // training residual  (FP32 native odd)
+    void* tmp32[2] = {};
+    int nsm = 0;
+};
+
+static size_t ptc_nw(const tm_ptc* n, int l) { return (size_t)9 * n->ch[l + 1] * n->ch[l] * 16; }
+
+static tm_status ptc_embed_all(tm_ptc* n, cudaStream_t st) {
+    for (int l = 0; l < n->L; ++l) CK(launch_ptc_embed_weights(n->W[l], n->ch[l], n->ch[l + 1], n->wf[l], n->wa[l], st));
+    return TM_OK;
+}
+
+extern "C" tm_status tm_ptc_create(tm_ptc** out, int nlayers, const int* channels, int device) {
+    if (!out || !channels || nlayers < 1 || nlayers > 8) return fail(TM_ERR_ARG, "tm_ptc_create: bad argument");
+    if (channels[0] != 1 || channels[nlayers] != 1)
+        return fail(TM_ERR_ARG, "tm_ptc_create: first and last channel counts must be 1");
+    for (int l = 0; l <= nlayers; ++l) {
+        const int c = channels[l];
+        if (c != 1 && c != 2 && c != 4 && c != 8) return fail(TM_ERR_ARG, "tm_ptc_create: channels must be 1, 2, 4 or 8");
+    }
+    for (int l = 0; l < nlayers; ++l) {
+        const int a = channels[l], b = channels[l + 1];
+        const bool ok = (a == 1 && (b == 1 || b == 2 || b == 4 || b == 8)) || (b == 1 && (a == 2 || a == 4 || a == 8)) ||
+                        (a == b);
+        if (!ok) return fail(TM_ERR_UNSUPPORTED, "tm_ptc_create: layer %d (%d -> %d) has no kernel", l, a, b);
+    }
+    CK(cudaSetDevice(device));
+    tm_ptc* n = new tm_ptc();
+    n->device = device;
+    n->L = nlayers;
+    for (int l = 0; l <= nlayers; ++l) n->ch[l] = channels[l];
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, device));
+    n->nsm = prop.multiProcessorCount;
+    for (int l = 0; l < nlayers; ++l) {
+        const size_t b = sizeof(float2) * ptc_nw(n, l);
+        CK(cudaMalloc(&n->W[l], b)); CK(cudaMemset(n->W[l], 0, b));
+        CK(cudaMalloc(&n->m[l], b)); CK(cudaMemset(n->m[l], 0, b));
+        CK(cudaMalloc(&n->v[l], b)); CK(cudaMemset(n->v[l], 0, b));
+        CK(cudaMalloc(&n->G[l], b)); CK(cudaMemset(n->G[l], 0, b));
+        CK(cudaMalloc(&n->wf[l], 2 * 9 * 64 * 64));
+        CK(cudaMalloc(&n->wa[l], 2 * 9 * 64 * 64));
+    }
+    n->nchunk = 4 * n->nsm;
+    CK(cudaMalloc(&n->wpart, sizeof(float) * 9 * 4096 * n->nchunk));
+    CK(cudaMalloc(&n->dscal, sizeof(double) * 8));
+    CK(cudaMallocHost(&n->hscal, sizeof(double) * 8));
+    CKS(ptc_embed_all(n, nullptr));
+    CK(cudaDeviceSynchronize());
+    *out = n;
+    return TM_OK;
+}
+
+static void ptc_free_acts(tm_ptc* n) {
+    for (auto& a : n->act) { cudaFree(a); a = nullptr; }
+    for (auto& d : n->del) { cudaFree(d); d = nullptr; }
+    cudaFree(n->dpart); n->dpart = nullptr;
+    cudaFree(n->e32); cudaFree(n->r32); cudaFree(n->tmp32[0]); cudaFree(n->tmp32[1]);
+    n->e32 = n->r32 = n->tmp32[0] = n->tmp32[1] = nullptr;
+    n->V = 0;
+}
+
+extern "C" tm_status tm_ptc_destroy(tm_ptc* n) {
+    if (!n) return TM_OK;
+    cudaSetDevice(n->device);
+    cudaDeviceSynchronize();
+    for (int l = 0; l < n->L; ++l) {
+        cudaFree(n->W[l]); cudaFree(n->m[l]); cudaFree(n->v[l]); cudaFree(n->G[l]);
+        cudaFree(n->wf[l]); cudaFree(n->wa[l]);
+    }
+    ptc_free_acts(n);
+    cudaFree(n->wpart);
+    cudaFree(n->dscal);
+    cudaFreeHost(n->hscal);
+    delete n;
+    return TM_OK;
+}
+
+static tm_status ptc_buffers(tm_ptc* n, const tm_ctx* c) {
+    const long V = 2 * c->vh;
+    if (n->V == V) return TM_OK;
+    ptc_free_acts(n);
+    for (int l = 0; l <= n->L; ++l) CK(cudaMalloc(&n->act[l], (size_t)n->ch[l] * 3 * 16 * V));
+    for (auto& d : n->del) CK(cudaMalloc(&d, (size_t)PTC_MAXC * 3 * 16 * V));
+    CK(cudaMalloc(&n->dpart, sizeof(double) * ((V + 255) / 256)));
+    const size_t s32 = spinor_bytes(P32, 12, c->vh);
+    CK(cudaMalloc(&n->e32, s32));
+    CK(cudaMalloc(&n->r32, s32));
+    CK(cudaMalloc(&n->tmp32[0], s32));
+    CK(cudaMalloc(&n->tmp32[1], s32));
+    n->V = V;
+    return TM_OK;
+}
+
+static PtcGeom ptc_geom(const tm_ctx* c) {
+    PtcGeom g{};
+    g.X = c->g.X; g.Y = c->g.Y; g.Z = c->g.Z; g.T = c->g.T;
+    g.vh = c->vh;
+    g.V = 2 * c->vh;
+    g.bc_t = (float)c->params.bc_t;
+    g.gauge[0] = c->gaugeP[PF16][0];
+    g.gauge[1] = c->gaugeP[PF16][1];
+    return g;
+}
+
+// weights canonical: complex FP64 [layer][path 9][cout][cin][4][4], host pointer
+extern "C" tm_status tm_ptc_set_weights(tm_ptc* n, const double* w) {
+    if (!n || !w) return fail(TM_ERR_ARG, "tm_ptc_set_weights: null argument");
+    CK(cudaSetDevice(n->device));
+    size_t off = 0;
+    for (int l = 0; l < n->L; ++l) {
+        const size_t cnt = ptc_nw(n, l);
+        std::vector<float2> h(cnt);
+        for (size_t k = 0; k < cnt; ++k) h[k] = make_float2((float)w[2 * (off + k)], (float)w[2 * (off + k) + 1]);
+        CK(cudaMemcpy(n->W[l], h.data(), sizeof(float2) * cnt, cudaMemcpyHostToDevice));
+        off += cnt;
+    }
+    CKS(ptc_embed_all(n, nullptr));
+    CK(cudaDeviceSynchronize());
+    return TM_OK;
+}
+
+extern "C" tm_status tm_ptc_get_weights(const tm_ptc* n, double* w) {
+    if (!n || !w) return fail(TM_ERR_ARG, "tm_ptc_get_weights: null argument");
+    CK(cudaSetDevice(n->device));
+    size_t off = 0;
+    for (int l = 0; l < n->L; ++l) {
+        const size_t cnt = ptc_nw(n, l);
+        std::vector<float2> h(cnt);
+        CK(cudaMemcpy(h.data(), n->W[l], sizeof(float2) * cnt, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < cnt; ++k) { w[2 * (off + k)] = h[k].x; w[2 * (off + k) + 1] = h[k].y; }
+        off += cnt;
+    }
+    return TM_OK;
+}
+
+extern "C" tm_status tm_ptc_num_weights(const tm_ptc* n, size_t* count) {
+    if (!n || !count) return fail(TM_ERR_ARG, "tm_ptc_num_weights: null argument");
+    size_t s = 0;
+    for (int l = 0; l < n->L; ++l) s += ptc_nw(n, l);
+    *count = s;
+    return TM_OK;
+}
+
+// z (FP32 native odd) = N(r) (FP32 native odd); activations kept in n->act
+static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaStream_t st) {
+    const PtcGeom g = ptc_geom(c);
+    CK(launch_ptc_embed_odd(P32, r, n->act[0], g, st));
+    for (int l = 0; l < n->L; ++l)
+        CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, st));
+    if (z) CK(launch_ptc_extract_odd(P32, n->act[n->L], z, g, st));
+    return TM_OK;
+}
+
+// loss of (r, e) with activations from ptc_forward(r); gradients accumulate into G (scaled)
+static tm_status ptc_backward(tm_ptc* n, tm_ctx* c, const void* e, float scale, cudaStream_t st) {
+    const PtcGeom g = ptc_geom(c);
+    CK(launch_ptc_loss_delta(n->act[n->L], e, n->del[0], g, n->dscal + 0, n->dpart, n->dscal + 1, st));
+    int cur = 0;
+    for (int l = n->L - 1; l >= 0; --l) {
+        CK(launch_ptc_wgrad(n->ch[l], n->ch[l + 1], g, n->act[l], n->del[cur], n->wpart, n->nchunk, n->G[l], scale, st));
+        if (l > 0) {
+            CK(launch_ptc_layer(n->ch[l + 1], n->ch[l], g, n->del[cur], n->del[1 - cur], n->wa[l], n->nsm, st));
+            cur = 1 - cur;
+        }
+    }
+    return TM_OK;
+}
+
+static tm_status ptc_prepare(tm_ptc* n, tm_ctx* c, cudaStream_t st) {
+    if (c->device != n->device) return fail(TM_ERR_ARG, "network and context on different devices");
+    CKS(ensure_prec(c, PF16, st));
+    CKS(ensure_prec(c, P32, st));
+    return ptc_buffers(n, c);
+}
+
+extern "C" tm_status tm_ptc_apply(tm_ptc* n, tm_ctx* c, void* out, const void* in, void* stream) {
+    if (!n || !c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_ptc_apply: bad argument");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ptc_prepare(n, c, st));
+    return ptc_forward(n, c, out, in, st);
+}
+
+// loss and gradient of one pair (canonical FP64 r, e, host or device); grad host, same layout as weights
+extern "C" tm_status tm_ptc_grad(tm_ptc* n, tm_ctx* c, const double* r, const double* e, double* loss, double* grad,
+                                 void* stream) {
+    if (!n || !c || !r || !e || !loss || !grad) return fail(TM_ERR_ARG, "tm_ptc_grad: null argument");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ptc_prepare(n, c, st));
+    void* b64;
+    CKS(ws_get(c, WS_B64, spinor_bytes(P64, 12, c->vh), &b64));
+    CKS(stage_in(c, 1, r, WS_STAGE_B, b64, st));
+    CK((launch_convert<P32, P64, 12, 1>(vb1(c, n->r32, b64), nblk(c->vh, BLAS_BS), st)));
+    CKS(stage_in(c, 1, e, WS_STAGE_B, b64, st));
+    CK((launch_convert<P32, P64, 12, 1>(vb1(c, n->e32, b64), nblk(c->vh, BLAS_BS), st)));
+    CK((launch_norm2<P32, 12, 1>(vb1(c, n->e32, nullptr, nullptr, nullptr, n->dscal + 0), nblk(c->vh, BLAS_BS), st)));
+    for (int l = 0; l < n->L; ++l) CK(cudaMemsetAsync(n->G[l], 0, sizeof(float2) * ptc_nw(n, l), st));
+    CKS(ptc_forward(n, c, nullptr, n->r32, st));
+    CKS(ptc_backward(n, c, n->e32, 1.0f, st));
+    CK(cudaMemcpyAsync(n->hscal, n->dscal, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *loss = n->hscal[1] / n->hscal[0];
+    size_t off = 0;
+    for (int l = 0; l < n->L; ++l) {
+        const size_t cnt = ptc_nw(n, l);
+        std::vector<float2> h(cnt);
+        CK(cudaMemcpy(h.data(), n->G[l], sizeof(float2) * cnt, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < cnt; ++k) { grad[2 * (off + k)] = h[k].x; grad[2 * (off + k) + 1] = h[k].y; }
+        off += cnt;
+    }
+    return TM_OK;
+}
+
+// Training on solver-generated pairs: e ~ complex Gaussian (Philox4x32-10 keyed by
+// seed, stream = pair index), r = A e with the FP32 operator of the pair's context
+// (pairs cycle through the contexts), loss ||N(r) - e||^2/||e||^2, Adam every
+// `batch` pairs on the mean gradient.  losses (host, npairs) receives every loss.
+extern "C" tm_status tm_ptc_train(tm_ptc* n, tm_ctx** cs, int nctx, tm_op op, int npairs, int batch, double lr,
+                                  unsigned long long seed, double* losses, void* stream) {
+    if (!n || !cs || nctx < 1 || npairs < 1 || batch < 1 || !(lr > 0)) return fail(TM_ERR_ARG, "tm_ptc_train: bad argument");
+    if (op != TM_MDAGM && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_ptc_train: light normal operator only");
+    for (int q = 0; q < nctx; ++q)
+        if (!cs[q] || cs[q]->vh != cs[0]->vh || cs[q]->device != n->device)
+            return fail(TM_ERR_ARG, "tm_ptc_train: contexts must share device and volume");
+    CK(cudaSetDevice(n->device));
+    const cudaStream_t st = S(stream);
+    for (int q = 0; q < nctx; ++q) CKS(ptc_prepare(n, cs[q], st));
+    double* dloss = nullptr;
+    CK(cudaMalloc(&dloss, sizeof(double) * 2 * npairs));
+    std::memset(cs[0]->h_ctl, 0, sizeof(SolverCtl));
+    for (int q = 0; q < nctx; ++q) {
+        std::memset(cs[q]->h_ctl, 0, sizeof(SolverCtl));
+        CKS(put_ctl(cs[q], st));
+    }
+    tm_status status = TM_OK;
+    for (int k = 0; k < npairs && status == TM_OK; ++k) {
+        tm_ctx* c = cs[k % nctx];
+        void *te, *mid;
+        CKS(ws_get(c, WS_TE_S, spinor_bytes(P32, 12, c->vh), &te));
+        CKS(ws_get(c, WS_MID_S, spinor_bytes(P32, 12, c->vh), &mid));
+        CK(launch_ptc_gauss_odd(n->e32, c->vh, seed, (unsigned long long)k, st));
+        CK((normal_op<P32, 1>(c, op, n->r32, n->e32, mid, te, st, nullptr, FIN_NONE)));
+        CK((launch_norm2<P32, 12, 1>(vb1(c, n->e32, nullptr, nullptr, nullptr, n->dscal + 0), nblk(c->vh, BLAS_BS), st)));
+        CKS(ptc_forward(n, c, nullptr, n->r32, st));
+        CKS(ptc_backward(n, c, n->e32, 1.0f / batch, st));
+        CK(cudaMemcpyAsync(dloss + 2 * k, n->dscal, sizeof(double) * 2, cudaMemcpyDeviceToDevice, st));
+        if ((k + 1) % batch == 0 || k + 1 == npairs) {
+            n->step += 1;
+            for (int l = 0; l < n->L; ++l)
+                CK(launch_ptc_adam(n->W[l], n->m[l], n->v[l], n->G[l], (int)ptc_nw(n, l), (float)lr, 0.9f, 0.999f,
+                                   1e-8f, n->step, st));
+            CKS(ptc_embed_all(n, st));
+        }
+    }
+    std::vector<double> h(2 * (size_t)npairs);
+    CK(cudaMemcpyAsync(h.data(), dloss, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    cudaFree(dloss);
+    if (losses)
+        for (int k = 0; k < npairs; ++k) losses[k] = h[2 * k + 1] / h[2 * k];
+    return status;
+}
+
+extern "C" tm_status tm_ptc_save(const tm_ptc* n, const char* path) {
+    if (!n || !path) return fail(TM_ERR_ARG, "tm_ptc_save: null argument");
+    CK(cudaSetDevice(n->device));
+    FILE* f = fopen(path, "wb");
+    if (!f) return fail(TM_ERR_ARG, "tm_ptc_save: cannot open %s", path);
+    const char magic[8] = {'T', 'M', 'P', 'T', 'C', '1', 0, 0};
+    fwrite(magic, 1, 8, f);
+    fwrite(&n->L, sizeof(int), 1, f);
+    fwrite(n->ch, sizeof(int), n->L + 1, f);
+    fwrite(&n->step, sizeof(int), 1, f);
+    for (int l = 0; l < n->L; ++l) {
+        const size_t cnt = ptc_nw(n, l);
+        std::vector<float2> h(cnt);
+        for (float2* src : {n->W[l], n->m[l], n->v[l]}) {
+            if (cudaMemcpy(h.data(), src, sizeof(float2) * cnt, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                fclose(f);
+                return fail(TM_ERR_CUDA, "tm_ptc_save: copy failed");
+            }
+            fwrite(h.data(), sizeof(float2), cnt, f);
+        }
+    }
+    fclose(f);
+    return TM_OK;
+}
+
+extern "C" tm_status tm_ptc_load(tm_ptc* n, const char* path) {
+    if (!n || !path) return fail(TM_ERR_ARG, "tm_ptc_load: null argument");
+    CK(cudaSetDevice(n->device));
+    FILE* f = fopen(path, "rb");
+    if (!f) return fail(TM_ERR_ARG, "tm_ptc_load: cannot open %s", path);
+    char magic[8];
+    int L = 0, ch[9] = {}, step = 0;
+    bool ok = fread(magic, 1, 8, f) == 8 && std::memcmp(magic, "TMPTC1", 6) == 0 && fread(&L, sizeof(int), 1, f) == 1 &&
+              L == n->L && fread(ch, sizeof(int), L + 1, f) == (size_t)(L + 1) && fread(&step, sizeof(int), 1, f) == 1;
+    for (int l = 0; ok && l <= L; ++l) ok = ch[l] == n->ch[l];
+    for (int l = 0; ok && l < n->L; ++l) {
+        const size_t cnt = ptc_nw(n, l);
+        std::vector<float2> h(cnt);
+        for (float2* dst : {n->W[l], n->m[l], n->v[l]}) {
+            ok = ok && fread(h.data(), sizeof(float2), cnt, f) == cnt;
+            if (ok) ok = cudaMemcpy(dst, h.data(), sizeof(float2) * cnt, cudaMemcpyHostToDevice) == cudaSuccess;
+        }
+    }
+    fclose(f);
+    if (!ok) return fail(TM_ERR_ARG, "tm_ptc_load: %s does not hold a network of this shape", path);
+    n->step = step;
+    CKS(ptc_embed_all(n, nullptr));
+    CK(cudaDeviceSynchronize());
+    return TM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// flexible CG with the network as preconditioner (Notay's FCG, truncation 1):
+//   z_k = N(r_k);  p_k = z_k - (<q_{k-1}, z_k> / <p_{k-1}, q_{k-1}>) p_{k-1};  q_k = A p_k;
+//   alpha = <p_k, r_k> / <p_k, q_k>;  x += alpha p_k;  r -= alpha q_k.
+// Vectors FP32, operator FP32, network BF16; every time the iterated residual has
+// dropped by `delta` the solution is folded into FP64 and r = b - A x is
+// recomputed with the FP64 operator (reliable update), restarting the recursion.
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve_params* sp, double* x,
+                                  const double* b, tm_solve_info* info, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !n || !sp || !x || !b || !info) return fail(TM_ERR_ARG, "tm_solve_fcg: null argument");
+    if (op != TM_MDAGM && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_solve_fcg: light normal operator only");
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ensure_prec(c, P64, st));
+    CKS(ptc_prepare(n, c, st));
+    const long vh = c->vh;
+    const int nb = nblk(vh, BLAS_BS);
+    const size_t s64 = spinor_bytes(P64, 12, vh), s32 = spinor_bytes(P32, 12, vh);
+    void *x64, *b64, *r64, *ax64, *te64, *mid64, *xs, *rs, *z, *p, *q, *po, *qo, *te, *mid;
+    CKS(ws_get(c, WS_X64, s64, &x64));
+    CKS(ws_get(c, WS_B64, s64, &b64));
+    CKS(ws_get(c, WS_R64, s64, &r64));
+    CKS(ws_get(c, WS_AX64, s64, &ax64));
+    CKS(ws_get(c, WS_TE64, s64, &te64));
+    CKS(ws_get(c, WS_MID64, s64, &mid64));
+    CKS(ws_get(c, WS_X_S, s32, &xs));
+    CKS(ws_get(c, WS_R_S, s32, &rs));
+    CKS(ws_get(c, WS_P_S, s32, &p));
+    CKS(ws_get(c, WS_AP_S, s32, &q));
+    CKS(ws_get(c, WS_TE_S, s32, &te));
+    CKS(ws_get(c, WS_MID_S, s32, &mid));
+    CKS(ws_get(c, WS_FCG_Z, s32, &z));
+    CKS(ws_get(c, WS_FCG_PO, s32, &po));
+    CKS(ws_get(c, WS_FCG_QO, s32, &qo));
+    CKS(stage_in(c, 1, b, WS_STAGE_B, b64, st));
+    CKS(stage_in(c, 1, x, WS_STAGE_X, x64, st));
+    const double tol = sp->tol > 0 ? sp->tol : 1e-10;
+    const int maxiter = sp->maxiter > 0 ? sp->maxiter : 10000;
+    const double delta = sp->delta > 0 ? sp->delta : 0.1;
+    double bb;
+    CKS((norm2_dev<P64, 12>(c, b64, st, &bb)));
+    info->iters = 0;
+    info->reliable_updates = 0;
+    if (!std::isfinite(bb)) return fail(TM_ERR_BREAKDOWN, "tm_solve_fcg: right-hand side is not finite");
+    double rr;
+    CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
+    const double target = tol * tol * bb;
+    std::memset(c->h_ctl, 0, sizeof(SolverCtl));
+    CKS(put_ctl(c, st));
+    double* d2 = c->d_scal + 2;
+    auto cdot = [&](const void* a, const void* bq, double* re, double* im) -> tm_status {
+        CK(launch_cdot32(a, bq, vh, c->partial, c->counter, d2, st));
+        CK(cudaMemcpyAsync(c->h_scal, d2, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        *re = c->h_scal[0];
+        *im = c->h_scal[1];
+        return TM_OK;
+    };
+    tm_status status = TM_OK;
+    int its = 0;
+    while (rr > target && bb > 0) {
+        // (re)start from the FP64 residual
+        CK((launch_convert<P32, P64, 12, 1>(vb1(c, rs, r64), nb, st)));
+        CK(cudaMemsetAsync(xs, 0, s32, st));
+        const double rr_start = rr;
+        double pq_old = 0.0;
+        bool first = true;
+        double rr_it = rr;
+        while (rr_it > std::max(target, delta * delta * rr_start) && its < maxiter) {
+            CKS(ptc_forward(n, c, z, rs, st));
+            if (first) {
+                CK(cudaMemcpyAsync(p, z, s32, cudaMemcpyDeviceToDevice, st));
+            } else {
+                double qr, qi;
+                CKS(cdot(qo, z, &qr, &qi));
+                // p = z + beta p_old, beta = -<q_old, z> / <p_old, q_old>
+                CK(cudaMemcpyAsync(p, po, s32, cudaMemcpyDeviceToDevice, st));
+                CK(launch_cxpay32(p, z, -qr / pq_old, -qi / pq_old, vh, st));
+            }
+            // q = A p with <p, q> = ||Q p||^2 fused
+            CK((normal_op<P32, 1>(c, op, q, p, mid, te, st, c->ctl, FIN_STORE)));
+            CK(cudaMemcpyAsync(c->h_scal + 4, &c->ctl->result, sizeof(double), cudaMemcpyDeviceToHost, st));
+            double pr, pi;
+            CKS(cdot(p, rs, &pr, &pi));
+            const double pq = c->h_scal[4];
+            if (!(pq > 0) || !std::isfinite(pq)) { status = TM_ERR_BREAKDOWN; break; }
+            const double ar = pr / pq, ai = pi / pq;
+            CK(launch_caxpy32(xs, p, ar, ai, vh, st));
+            CK(launch_caxpy32(rs, q, -ar, -ai, vh, st));
+            CK(cudaMemcpyAsync(po, p, s32, cudaMemcpyDeviceToDevice, st));
+            CK(cudaMemcpyAsync(qo, q, s32, cudaMemcpyDeviceToDevice, st));
+            pq_old = pq;
+            first = false;
+            ++its;
+            CKS((norm2_dev<P32, 12>(c, rs, st, &rr_it)));
+            if (!std::isfinite(rr_it)) { status = TM_ERR_BREAKDOWN; break; }
+        }
+        if (status != TM_OK) break;
+        CK((launch_add_to64<P32, 12, 1>(vb1(c, x64, xs), nb, st)));
+        CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
+        info->reliable_updates += 1;
+        if (its >= maxiter && rr > target) { status = TM_ERR_NOT_CONVERGED; break; }
+    }
+    info->iters = its;
+    info->true_rel_res = bb > 0 ? std::sqrt(rr / bb) : 0.0;
+    info->status = status;
+    CKS(stage_out(c, 1, x, WS_STAGE_X, x64, st));
+    CK(cudaStreamSynchronize(st));
+    info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (status != TM_OK) return fail(status, "tm_solve_fcg: %s", status == TM_ERR_BREAKDOWN ? "breakdown" : "not converged");
+    return TM_OK;
 }

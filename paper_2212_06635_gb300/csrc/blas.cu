@@ -422,3 +422,96 @@ template cudaError_t launch_normalize64<12>(const VecBatch<1>&, int, cudaStream_
 template cudaError_t launch_normalize64<24>(const VecBatch<1>&, int, cudaStream_t);
 
 }  // namespace tmk
+
+// ---------------------------------------------------------------------------
+// complex BLAS-1 for flexible CG (FP32 native light fields)
+// ---------------------------------------------------------------------------
+namespace tmk {
+
+// <a, b> = sum conj(a) b -> dst2[0] (re), dst2[1] (im); deterministic two-level sum
+__global__ void __launch_bounds__(BLAS_BS) k_cdot32(const void* a, const void* b, long vh, double* partial,
+                                                    unsigned int* counter, double* dst2) {
+    __shared__ double sh[BLAS_BS / 32];
+    __shared__ int am_last;
+    const long i = (long)blockIdx.x * BLAS_BS + threadIdx.x;
+    double re = 0.0, im = 0.0;
+    if (i < vh) {
+        cpx<float> x[12], y[12];
+        load_spinor<P32, 12>(a, vh, i, x);
+        load_spinor<P32, 12>(b, vh, i, y);
+        float r = 0.f, m = 0.f;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            r += x[q].re * y[q].re + x[q].im * y[q].im;
+            m += x[q].re * y[q].im - x[q].im * y[q].re;
+        }
+        re = r;
+        im = m;
+    }
+    re = block_sum<BLAS_BS>(re, sh);
+    im = block_sum<BLAS_BS>(im, sh);
+    const int nb = gridDim.x;
+    if (threadIdx.x == 0) {
+        partial[2 * blockIdx.x] = re;
+        partial[2 * blockIdx.x + 1] = im;
+        __threadfence();
+        am_last = atomicAdd(counter, 1u) == (unsigned)(nb - 1);
+    }
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    double tr = 0.0, ti = 0.0;
+    for (int k = threadIdx.x; k < nb; k += BLAS_BS) {
+        tr += ((volatile double*)partial)[2 * k];
+        ti += ((volatile double*)partial)[2 * k + 1];
+    }
+    tr = block_sum<BLAS_BS>(tr, sh);
+    ti = block_sum<BLAS_BS>(ti, sh);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        dst2[0] = tr;
+        dst2[1] = ti;
+    }
+}
+
+// y += (ar + i ai) x
+__global__ void __launch_bounds__(BLAS_BS) k_caxpy32(void* y, const void* x, float ar, float ai, long vh) {
+    const long i = (long)blockIdx.x * BLAS_BS + threadIdx.x;
+    if (i >= vh) return;
+    cpx<float> a[12], b[12];
+    load_spinor<P32, 12>(y, vh, i, a);
+    load_spinor<P32, 12>(x, vh, i, b);
+    const cpx<float> s = C(ar, ai);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) cfma(a[q], s, b[q]);
+    store_spinor<P32, 12>(y, vh, i, a);
+}
+
+// y = x + (br + i bi) y
+__global__ void __launch_bounds__(BLAS_BS) k_cxpay32(void* y, const void* x, float br, float bi, long vh) {
+    const long i = (long)blockIdx.x * BLAS_BS + threadIdx.x;
+    if (i >= vh) return;
+    cpx<float> a[12], b[12];
+    load_spinor<P32, 12>(y, vh, i, a);
+    load_spinor<P32, 12>(x, vh, i, b);
+    const cpx<float> s = C(br, bi);
+#pragma unroll
+    for (int q = 0; q < 12; ++q) a[q] = b[q] + s * a[q];
+    store_spinor<P32, 12>(y, vh, i, a);
+}
+
+cudaError_t launch_cdot32(const void* a, const void* b, long vh, double* partial, unsigned int* counter,
+                          double* dst2, cudaStream_t st) {
+    k_cdot32<<<(unsigned)((vh + BLAS_BS - 1) / BLAS_BS), BLAS_BS, 0, st>>>(a, b, vh, partial, counter, dst2);
+    return cudaGetLastError();
+}
+cudaError_t launch_caxpy32(void* y, const void* x, double ar, double ai, long vh, cudaStream_t st) {
+    k_caxpy32<<<(unsigned)((vh + BLAS_BS - 1) / BLAS_BS), BLAS_BS, 0, st>>>(y, x, (float)ar, (float)ai, vh);
+    return cudaGetLastError();
+}
+cudaError_t launch_cxpay32(void* y, const void* x, double br, double bi, long vh, cudaStream_t st) {
+    k_cxpay32<<<(unsigned)((vh + BLAS_BS - 1) / BLAS_BS), BLAS_BS, 0, st>>>(y, x, (float)br, (float)bi, vh);
+    return cudaGetLastError();
+}
+
+}  // namespace tmk

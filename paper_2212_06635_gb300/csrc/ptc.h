@@ -1,0 +1,41 @@
+// Device geometry and launchers of the parallel-transport network kernels (ptc.cu).
+#pragma once
+
+#include "tm_internal.h"
+
+namespace tmk {
+
+constexpr int PTC_TILE = 32;               // sites per tile
+constexpr int PTC_BS = 128;                // threads per block (4 warps)
+constexpr int PTC_N = 3 * PTC_TILE;        // GEMM columns per tile (site, colour)
+constexpr int PTC_MAXC = 8;                // channels per layer
+
+struct PtcGeom {
+    int X, Y, Z, T;
+    long V, vh;
+    float bc_t;
+    const void* gauge[2];   // FP16 native links per parity
+};
+
+cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* wemb,
+                             int nsm, cudaStream_t st);
+cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
+                             int nchunk, float2* grad, float scale, cudaStream_t st);
+cudaError_t launch_ptc_embed_weights(const float2* W, int cin, int cout, void* fwd, void* adj, cudaStream_t st);
+cudaError_t launch_ptc_adam(float2* W, float2* m, float2* v, float2* grad, int n, float lr, float b1, float b2,
+                            float eps, int step, cudaStream_t st);
+cudaError_t launch_ptc_embed_odd(int prec, const void* r, void* a0, const PtcGeom& g, cudaStream_t st);
+cudaError_t launch_ptc_extract_odd(int prec, const void* a, void* z, const PtcGeom& g, cudaStream_t st);
+// loss sum ||z - e||^2 -> *out, delta = (z - e) / *ee on odd sites (0 elsewhere)
+cudaError_t launch_ptc_loss_delta(const void* aL, const void* e, void* delta, const PtcGeom& g, const double* ee,
+                                  double* partial, double* out, cudaStream_t st);
+cudaError_t launch_ptc_gauss_odd(void* e, long vh, unsigned long long seed, unsigned long long stream,
+                                 cudaStream_t st);
+
+// complex BLAS-1 used by flexible CG (single problem, FP32 fields)
+cudaError_t launch_cdot32(const void* a, const void* b, long vh, double* partial, unsigned int* counter,
+                          double* dst2, cudaStream_t st);
+cudaError_t launch_caxpy32(void* y, const void* x, double ar, double ai, long vh, cudaStream_t st);
+cudaError_t launch_cxpay32(void* y, const void* x, double br, double bi, long vh, cudaStream_t st);
+
+}  // namespace tmk
