@@ -176,6 +176,55 @@ tm_status tm_power_iteration(tm_ctx* ctx, tm_op op, int iters, double* lambda_ma
 tm_status tm_kernel_times(tm_ctx* ctx, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
                           void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned preconditioner: gauge-equivariant parallel-transport network (PTC).
+ * Not in the paper, which preconditions its hardest solves by multigrid
+ * (Sec. 4.1); the network stands in for it inside flexible CG.  Layer l maps
+ * channels[l] -> channels[l+1] spinor fields on the full lattice:
+ *   out^a(x) = sum_{p} sum_b W_p^{ab} (T_p in^b)(x),  p in {1, +x,+y,+z,+t, -x,-y,-z,-t},
+ *   (T_{+mu} f)(x) = U_mu(x) f(x+mu),  (T_{-mu} f)(x) = U_mu(x-mu)^+ f(x-mu),
+ * W_p^{ab} a complex 4x4 spin matrix; no activation (the preconditioner is a
+ * linear map).  The input is the odd-site residual embedded with zeros on even
+ * sites; the output is the odd sites of the last layer.  Channel mixing runs on
+ * the tensor cores in BF16 with FP32 accumulation; activations are BF16.
+ * Canonical weights: complex FP64 [layer][path 9][c_out][c_in][4][4], host memory.
+ * ------------------------------------------------------------------------- */
+typedef struct tm_ptc tm_ptc;
+
+/* channels has nlayers+1 entries, first and last 1, each 1, 2, 4 or 8 (the
+ * layer shapes 1->c, c->c, c->1).  Weights start at zero. */
+tm_status tm_ptc_create(tm_ptc** net, int nlayers, const int* channels, int device);
+tm_status tm_ptc_destroy(tm_ptc* net);
+tm_status tm_ptc_num_weights(const tm_ptc* net, size_t* complex_count);
+tm_status tm_ptc_set_weights(tm_ptc* net, const double* weights);
+/* Start near the identity: path 1 carries scale * 1 between equal channel
+ * indices, every other weight is uniform noise in [-noise, noise] (re, im) from
+ * a seeded splitmix64 stream; resets the Adam state. */
+tm_status tm_ptc_init(tm_ptc* net, double scale, double noise, unsigned long long seed);
+tm_status tm_ptc_get_weights(const tm_ptc* net, double* weights);
+/* out = N(in): native FP32 light odd fields of ctx's lattice (device), stream-ordered. */
+tm_status tm_ptc_apply(tm_ptc* net, tm_ctx* ctx, void* out, const void* in, void* stream);
+/* Loss L = ||N(r) - e||^2 / ||e||^2 of one pair (canonical FP64 r, e; host or
+ * device) and its Wirtinger gradient dL/dconj(W) (host, canonical weight layout). */
+tm_status tm_ptc_grad(tm_ptc* net, tm_ctx* ctx, const double* r, const double* e, double* loss,
+                      double* grad, void* stream);
+/* Train on npairs solver-generated pairs: e ~ complex Gaussian (Philox4x32-10
+ * keyed by seed, one stream per pair), r = A e with the FP32 operator op
+ * (TM_MDAGM or TM_QPQM) of ctxs[k % nctx] (same volume), Adam (lr, 0.9, 0.999)
+ * on the mean gradient of every `batch` pairs.  losses: host array of npairs or NULL. */
+tm_status tm_ptc_train(tm_ptc* net, tm_ctx** ctxs, int nctx, tm_op op, int npairs, int batch, double lr,
+                       unsigned long long seed, double* losses, void* stream);
+/* Checkpoint: weights and Adam state to / from a binary file. */
+tm_status tm_ptc_save(const tm_ptc* net, const char* path);
+tm_status tm_ptc_load(tm_ptc* net, const char* path);
+
+/* Flexible CG (truncation 1) on A = TM_MDAGM or TM_QPQM, preconditioned by net;
+ * FP32 vectors and operator, BF16 network, FP64 reliable updates (sp->delta)
+ * restarting the recursion; stops at FP64 true relative residual sp->tol.
+ * x, b canonical FP64 (host or device); sp->sloppy is ignored. */
+tm_status tm_solve_fcg(tm_ctx* ctx, tm_op op, tm_ptc* net, const tm_solve_params* sp, double* x,
+                       const double* b, tm_solve_info* info, void* stream);
+
 /* Stencil kernel variant of each pass of the Schur operator for one storage
  * precision and flavour count: 0 = direct (operands loaded into registers),
  * 1 = shared-memory staged (asynchronous copies of the neighbour spinors, links

@@ -1541,6 +1541,45 @@ extern "C" tm_status tm_ptc_num_weights(const tm_ptc* n, size_t* count) {
     return TM_OK;
 }
 
+// Initial weights: the identity path carries scale * 1 between equal channel
+// indices (a product of L layers then maps r to scale^L r), every other weight is
+// uniform noise in [-noise, noise] (re and im) from splitmix64 seeded by `seed`.
+extern "C" tm_status tm_ptc_init(tm_ptc* n, double scale, double noise, unsigned long long seed) {
+    if (!n) return fail(TM_ERR_ARG, "tm_ptc_init: null argument");
+    size_t total = 0;
+    for (int l = 0; l < n->L; ++l) total += ptc_nw(n, l);
+    std::vector<double> w(2 * total);
+    uint64_t s = seed * 0x9e3779b97f4a7c15ull + 1;
+    auto uni = [&]() {
+        uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+        z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+        z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+        z ^= z >> 31;
+        return (double)(z >> 11) * (1.0 / 9007199254740992.0) * 2.0 - 1.0;
+    };
+    size_t off = 0;
+    for (int l = 0; l < n->L; ++l) {
+        const int ci = n->ch[l], co = n->ch[l + 1];
+        for (int p = 0; p < 9; ++p)
+            for (int a = 0; a < co; ++a)
+                for (int b = 0; b < ci; ++b)
+                    for (int si = 0; si < 4; ++si)
+                        for (int t = 0; t < 4; ++t) {
+                            const size_t k = off + ((((size_t)p * co + a) * ci + b) * 4 + si) * 4 + t;
+                            w[2 * k] = noise * uni();
+                            w[2 * k + 1] = noise * uni();
+                            if (p == 0 && a == b && si == t) w[2 * k] += scale;
+                        }
+        off += ptc_nw(n, l);
+    }
+    n->step = 0;
+    for (int l = 0; l < n->L; ++l) {
+        CK(cudaMemset(n->m[l], 0, sizeof(float2) * ptc_nw(n, l)));
+        CK(cudaMemset(n->v[l], 0, sizeof(float2) * ptc_nw(n, l)));
+    }
+    return tm_ptc_set_weights(n, w.data());
+}
+
 // z (FP32 native odd) = N(r) (FP32 native odd); activations kept in n->act
 static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaStream_t st) {
     const PtcGeom g = ptc_geom(c);
@@ -1828,3 +1867,4 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     if (status != TM_OK) return fail(status, "tm_solve_fcg: %s", status == TM_ERR_BREAKDOWN ? "breakdown" : "not converged");
     return TM_OK;
 }
+

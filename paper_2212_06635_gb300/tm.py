@@ -82,6 +82,19 @@ _sigs = {
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_ptc_create": [ct.POINTER(_vp), ct.c_int, ct.POINTER(ct.c_int), ct.c_int],
+    "tm_ptc_destroy": [_vp],
+    "tm_ptc_num_weights": [_vp, ct.POINTER(ct.c_size_t)],
+    "tm_ptc_set_weights": [_vp, _vp],
+    "tm_ptc_init": [_vp, ct.c_double, ct.c_double, ct.c_ulonglong],
+    "tm_ptc_get_weights": [_vp, _vp],
+    "tm_ptc_apply": [_vp, _vp, _vp, _vp, _vp],
+    "tm_ptc_grad": [_vp, _vp, _vp, _vp, ct.POINTER(ct.c_double), _vp, _vp],
+    "tm_ptc_train": [_vp, ct.POINTER(_vp), ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_ulonglong,
+                     _vp, _vp],
+    "tm_ptc_save": [_vp, ct.c_char_p],
+    "tm_ptc_load": [_vp, ct.c_char_p],
+    "tm_solve_fcg": [_vp, ct.c_int, _vp, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
     "tm_autotune": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning), _vp],
     "tm_set_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
     "tm_get_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
@@ -248,3 +261,72 @@ def tm_get_tuning(ctx, prec, nflavour=1):
     t = tm_tuning()
     _check(lib.tm_get_tuning(ctx, int(prec), int(nflavour), ct.byref(t)))
     return t.even_pass, t.odd_pass
+
+
+# --- learned preconditioner ----------------------------------------------------
+def tm_ptc_create(channels, device=0):
+    h = _vp()
+    ch = (ct.c_int * len(channels))(*[int(c) for c in channels])
+    _check(lib.tm_ptc_create(ct.byref(h), len(channels) - 1, ch, int(device)))
+    return h.value
+
+
+def tm_ptc_destroy(net):
+    _check(lib.tm_ptc_destroy(net))
+
+
+def tm_ptc_num_weights(net):
+    n = ct.c_size_t()
+    _check(lib.tm_ptc_num_weights(net, ct.byref(n)))
+    return n.value
+
+
+def tm_ptc_set_weights(net, w):
+    """w: complex128 array, canonical layout, flattened in layer order."""
+    a = np.ascontiguousarray(w, dtype=np.complex128)
+    _check(lib.tm_ptc_set_weights(net, a.ctypes.data))
+
+
+def tm_ptc_init(net, scale=0.5, noise=0.01, seed=4000):
+    _check(lib.tm_ptc_init(net, float(scale), float(noise), int(seed)))
+
+
+def tm_ptc_get_weights(net):
+    a = np.empty(tm_ptc_num_weights(net), dtype=np.complex128)
+    _check(lib.tm_ptc_get_weights(net, a.ctypes.data))
+    return a
+
+
+def tm_ptc_apply(net, ctx, out, inp, stream=None):
+    _check(lib.tm_ptc_apply(net, ctx, ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_ptc_grad(net, ctx, r, e, stream=None):
+    loss = ct.c_double()
+    g = np.empty(tm_ptc_num_weights(net), dtype=np.complex128)
+    _check(lib.tm_ptc_grad(net, ctx, ptr(r), ptr(e), ct.byref(loss), g.ctypes.data, _stream(stream)))
+    return loss.value, g
+
+
+def tm_ptc_train(net, ctxs, op, npairs, batch=1, lr=1e-3, seed=5000, stream=None):
+    cp = (_vp * len(ctxs))(*ctxs)
+    losses = np.empty(npairs, dtype=np.float64)
+    _check(lib.tm_ptc_train(net, cp, len(ctxs), int(op), int(npairs), int(batch), float(lr), int(seed),
+                            losses.ctypes.data, _stream(stream)))
+    return losses
+
+
+def tm_ptc_save(net, path):
+    _check(lib.tm_ptc_save(net, str(path).encode()))
+
+
+def tm_ptc_load(net, path):
+    _check(lib.tm_ptc_load(net, str(path).encode()))
+
+
+def tm_solve_fcg(ctx, op, net, sp, x, b, stream=None, check=True):
+    info = tm_solve_info()
+    st = lib.tm_solve_fcg(ctx, int(op), net, ct.byref(sp), ptr(x), ptr(b), ct.byref(info), _stream(stream))
+    if check:
+        _check(st)
+    return info
