@@ -137,6 +137,22 @@ tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_c
 tm_status tm_field_norm2(tm_ctx* ctx, tm_prec prec, int nflavour, const void* field, double* result,
                          void* stream);
 
+/* Allocation-free variant of tm_field_norm2, for callers that may not allocate
+ * device memory at call time (code running during CUDA-graph stream capture,
+ * latency-critical loops that must not reach the allocator, frameworks that own
+ * the device memory budget).  The paper has no counterpart: this is a library
+ * service, not part of the method.  Same arguments, result and reduction order
+ * as tm_field_norm2, but the block partials live in a fixed array in the
+ * library's device memory (about 512 KB, held by every GPU that loads the
+ * library until exit) instead of the context's scratch.  Limit: at most
+ * 16,777,216 sites per parity (TM_ERR_ARG beyond).  The first call on a device
+ * looks up that array's device address, so make the first call before any stream
+ * capture.  All calls share the array: calls whose executions overlap on the GPU
+ * (different streams, or different contexts on one device) race and give wrong
+ * results.  Allocates nothing. */
+tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, const void* field,
+                                 double* result, void* stream);
+
 /* out = op(in), native fields of precision prec on the device (eq:hQpm / eq:hQh).
  * Light ops take nflavour-1 fields, heavy ops nflavour-2 fields.  out != in.
  * Returns TM_ERR_STALE if the clover term predates the gauge field. */

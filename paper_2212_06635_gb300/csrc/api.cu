@@ -1868,3 +1868,7 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     return TM_OK;
 }
 
+namespace tmk {
+// record an error message for tm_last_error from another translation unit
+tm_status tmk_fail_msg(tm_status s, const char* msg) { return fail(s, "%s", msg); }
+}  // namespace tmk

@@ -82,6 +82,7 @@ _sigs = {
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_field_norm2_noalloc": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_ptc_create": [ct.POINTER(_vp), ct.c_int, ct.POINTER(ct.c_int), ct.c_int],
     "tm_ptc_destroy": [_vp],
     "tm_ptc_num_weights": [_vp, ct.POINTER(ct.c_size_t)],
@@ -193,6 +194,11 @@ def tm_field_export(ctx, prec, nflavour, dst, src, stream=None):
 def tm_field_norm2(ctx, prec, nflavour, field, result, stream=None):
     """result: device tensor with at least one float64 element."""
     _check(lib.tm_field_norm2(ctx, int(prec), int(nflavour), ptr(field), ptr(result), _stream(stream)))
+
+
+def tm_field_norm2_noalloc(ctx, prec, nflavour, field, result, stream=None):
+    """Allocation-free tm_field_norm2 (see include/tm.h); result: device float64 tensor."""
+    _check(lib.tm_field_norm2_noalloc(ctx, int(prec), int(nflavour), ptr(field), ptr(result), _stream(stream)))
 
 
 def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
