@@ -43,13 +43,15 @@ ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
 
 def mhat_bytes_per_site(prec):
     """Algorithmic bytes of one M_hat application per odd site (each field read or
-    written once per pass): even pass links 8x18 + psi 24 + inverse blocks 144 +
-    t_e 24 reals, odd pass links 144 + t_e 24 + psi 24 + clover 72 + out 24 reals;
-    16-bit spinors add one FP32 scale per site per spinor access."""
+    written once per pass): even pass 8 links + psi 24 + inverse blocks 144 +
+    t_e 24 reals, odd pass 8 links + t_e 24 + psi 24 + clover 72 + out 24 reals.
+    A link is 18 reals in FP64 and 12 (two rows) in FP32 / 16-bit storage; 16-bit
+    spinors add one FP32 scale per site per spinor access."""
     esz = ESZ[prec]
     scale = 4 if prec in (2, 3) else 0
-    k1 = 336 * esz + 2 * scale
-    k2 = 288 * esz + 3 * scale
+    links = 8 * (18 if prec == 0 else 12)
+    k1 = (links + 192) * esz + 2 * scale
+    k2 = (links + 144) * esz + 3 * scale
     return k1, k2
 
 
@@ -110,15 +112,26 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
+KERNEL_SOURCES = ["tm_internal.h", "tm_kernels.h", "dslash_common.cuh", "dslash.cu", "dslash_staged.cu"]
+
+
+def kernel_sources_sha256():
+    """Hash of every source the stencil kernels are compiled from."""
+    h = hashlib.sha256()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2212_06635_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()
+
+
 def traffic_from_profile(kernel_tag):
     """DRAM bytes per launch recorded by ncu for the current kernel source, else None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
             rec = json.load(f)
-        src = open(os.path.join(ROOT, "paper_2212_06635_gb300", "csrc", "dslash.cu"), "rb").read()
         entry = rec.get(kernel_tag)
-        if entry and entry.get("dslash_sha256") == hashlib.sha256(src).hexdigest():
+        if entry and entry.get("kernel_sources_sha256") == kernel_sources_sha256():
             return float(entry["dram_bytes_per_launch_full_size"])
     except Exception:
         pass
@@ -189,6 +202,7 @@ def run_ours(args, rank, world, local_rank):
     try:
         tm.tm_gauge_load(ctx, u, 1.0)
         tm.tm_clover_compute(ctx, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
+        tuning = tm.tm_autotune(ctx, prec, 1)
         bd = torch.from_numpy(b.view(np.float64).copy()).to(dev)
         nbytes = tm.tm_field_bytes(ctx, prec, 1)
         fin = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -280,6 +294,13 @@ def run_ours(args, rank, world, local_rank):
     finally:
         tm.tm_destroy(ctx)
 
+    extra = {}
+    if rank == 0 and not args.no_extra:
+        extra["multishift_heavy_24x48"] = run_multishift(tm, args)
+        extra["batch_uneven_24"] = run_batch(tm, args)
+    if rank == 0 and args.ptc:
+        extra["ptc_fcg_48x96"] = run_ptc(tm, args)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         gbs, sec = cpu_oracle_steps(3)
@@ -307,9 +328,155 @@ def run_ours(args, rank, world, local_rank):
                     "d2h_bytes_per_step": vh * 24 * 8},
             "gpu_launches": 4 * args.steps,
             "clocks": clocks,
+            "tuning": {"even_pass": "staged" if tuning[0] else "direct",
+                       "odd_pass": "staged" if tuning[1] else "direct"},
+            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+def _sync():
+    import torch
+    torch.cuda.synchronize()
+
+
+def run_multishift(tm, args):
+    """Heavy doublet 24^3x48: 12 shifts log-spaced in [1e-5, 1] x the spectral bound of
+    Q_h Q_h^dag; multishift CG in the sloppy precision with shift-by-shift
+    refinement to 1e-10, against multishift CG in FP64 throughout."""
+    import torch
+    w = CFG.HEAVY_24
+    u = F.gauge_field(w.dims, w.link_seed)
+    b = F.odd_spinor(w.dims, w.rhs_seed, 2)
+    ctx = tm.tm_create(w.dims, 0)
+    out = {"workload": w.name, "lattice": list(w.dims), "mubar": w.mubar, "epsbar": w.epsbar}
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, w.kappa, w.csw, mubar=w.mubar, epsbar=w.epsbar, bc_t=w.bc_t)
+        for p in (tm.TM_F32, tm.TM_F16):
+            tm.tm_autotune(ctx, p, 2)
+        t0 = time.perf_counter()
+        lam = tm.tm_power_iteration(ctx, tm.TM_QH_SQ, 100)
+        out["power_iteration_s"] = round(time.perf_counter() - t0, 4)
+        lam_t = 1.02 * lam
+        shifts = [lam_t * 10.0 ** (-5 + 5 * k / 11) for k in range(CFG.N_SHIFTS)]
+        out["lambda_max"] = lam
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        for name, sl in (("single_refined", tm.TM_F32), ("half_refined", tm.TM_F16), ("double", tm.TM_F64)):
+            xs = [torch.zeros_like(bd) for _ in shifts]
+            _sync()
+            t0 = time.perf_counter()
+            infos = tm.tm_solve_multishift(ctx, tm.TM_QH_SQ, shifts, xs, bd, tm.solve_params(tol=w.tol, sloppy=sl),
+                                           check=False)
+            _sync()
+            out[name] = {"seconds": round(time.perf_counter() - t0, 4),
+                         "max_true_rel_res": max(i.true_rel_res for i in infos),
+                         "iters_per_shift": [i.iters for i in infos],
+                         "status": sorted({tm.STATUS_NAMES[i.status] for i in infos})}
+    finally:
+        tm.tm_destroy(ctx)
+    return out
+
+
+def run_batch(tm, args):
+    """24 light solves on 8^3x16, 12^3x24, 16^3x32 and 24^3x48 (6 each) advanced
+    together by batched kernels, against the same 24 solves one after another."""
+    import torch
+    ws = CFG.batch_workloads()
+    ctxs, bs, xs = [], [], []
+    out = {"problems": len(ws), "lattices": sorted({"x".join(map(str, w.dims)) for w in ws})}
+    try:
+        for w in ws:
+            c = tm.tm_create(w.dims, 0)
+            ctxs.append(c)
+            tm.tm_gauge_load(c, F.gauge_field(w.dims, w.link_seed, workers=1), 1.0)
+            tm.tm_clover_compute(c, w.kappa, w.csw, mu=w.mu, bc_t=w.bc_t)
+            tm.tm_autotune(c, tm.TM_F16, 1)
+            b = F.odd_spinor(w.dims, w.rhs_seed)
+            bs.append(torch.from_numpy(b.view(np.float64).copy()).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        sp = tm.solve_params(tol=1e-10, sloppy=tm.TM_F16)
+        _sync()
+        t0 = time.perf_counter()
+        infos = tm.tm_solve_batch(ctxs, tm.TM_MDAGM, sp, xs, bs, check=False)
+        _sync()
+        out["batched_s"] = round(time.perf_counter() - t0, 4)
+        out["batched_max_true_rel_res"] = max(i.true_rel_res for i in infos)
+        out["batched_status"] = sorted({tm.STATUS_NAMES[i.status] for i in infos})
+        for x in xs:
+            x.zero_()
+        _sync()
+        t0 = time.perf_counter()
+        seq = [tm.tm_solve_cg(c, tm.TM_MDAGM, sp, x, b, check=False) for c, x, b in zip(ctxs, xs, bs)]
+        _sync()
+        out["sequential_s"] = round(time.perf_counter() - t0, 4)
+        out["sequential_max_true_rel_res"] = max(i.true_rel_res for i in seq)
+        out["speedup_batched_vs_sequential"] = round(out["sequential_s"] / out["batched_s"], 3)
+        out["iters"] = [i.iters for i in infos]
+    finally:
+        for c in ctxs:
+            tm.tm_destroy(c)
+    return out
+
+
+def run_ptc(tm, args):
+    """48^3x96: train the 4-layer 8-channel PTC network on solver-generated pairs
+    from several seeded configurations, then solve on the benchmark configuration
+    with PTC-preconditioned flexible CG vs mixed-precision CG vs FP64 CG."""
+    import torch
+    w = CFG.PTC_48
+    out = {"workload": w.name, "lattice": list(w.dims), "channels": [1, 8, 8, 8, 1]}
+    net = tm.tm_ptc_create([1, 8, 8, 8, 1])
+    ctxs = []
+    try:
+        tm.tm_ptc_init(net, scale=0.5, noise=0.02, seed=4000)
+        # one configuration resident at a time (a 48^3x96 context holds ~45 GB);
+        # the Adam state lives in the network, so training continues across them
+        per = max(1, args.ptc_pairs // args.ptc_configs)
+        setup_s, train_s, losses = 0.0, 0.0, []
+        for j in range(args.ptc_configs):
+            t0 = time.perf_counter()
+            c = tm.tm_create(w.dims, 0)
+            ctxs.append(c)
+            tm.tm_gauge_load(c, F.gauge_field(w.dims, 4000 + j), 1.0)
+            tm.tm_clover_compute(c, w.kappa, w.csw, mu=w.mu, bc_t=w.bc_t)
+            _sync()
+            t1 = time.perf_counter()
+            losses.append(tm.tm_ptc_train(net, [c], tm.TM_MDAGM, npairs=per, batch=8, lr=2e-3, seed=5000 + 1000 * j))
+            _sync()
+            t2 = time.perf_counter()
+            setup_s += t1 - t0
+            train_s += t2 - t1
+            tm.tm_destroy(c)
+            ctxs.pop()
+        losses = np.concatenate(losses)
+        out["config_setup_s"] = round(setup_s, 2)
+        out["train_s"] = round(train_s, 2)
+        out["train_pairs"] = int(len(losses))
+        out["loss_first64"] = float(np.mean(losses[:64]))
+        out["loss_last64"] = float(np.mean(losses[-64:]))
+        c = tm.tm_create(w.dims, 0)
+        ctxs.append(c)
+        tm.tm_gauge_load(c, F.gauge_field(w.dims, w.link_seed), 1.0)
+        tm.tm_clover_compute(c, w.kappa, w.csw, mu=w.mu, bc_t=w.bc_t)
+        tm.tm_autotune(c, tm.TM_F16, 1)
+        b = F.odd_spinor(w.dims, w.rhs_seed)
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        x = torch.zeros_like(bd)
+        info = tm.tm_solve_fcg(c, tm.TM_MDAGM, net, tm.solve_params(tol=w.tol), x, bd, check=False)
+        out["ptc_fcg"] = info.as_dict()
+        for name, sl in (("mixed_cg_f16", tm.TM_F16), ("fp64_cg", tm.TM_F64)):
+            x.zero_()
+            inf = tm.tm_solve_cg(c, tm.TM_MDAGM, tm.solve_params(tol=w.tol, sloppy=sl), x, bd, check=False)
+            out[name] = inf.as_dict()
+        out["speedup_ptc_fcg_vs_fp64_cg"] = round(out["fp64_cg"]["seconds"] / out["ptc_fcg"]["seconds"], 3)
+        out["speedup_ptc_fcg_vs_mixed_cg"] = round(out["mixed_cg_f16"]["seconds"] / out["ptc_fcg"]["seconds"], 3)
+    finally:
+        tm.tm_ptc_destroy(net)
+        for c in ctxs:
+            tm.tm_destroy(c)
+    return out
 
 
 def main():
@@ -323,6 +490,12 @@ def main():
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG time-to-solution leg")
     ap.add_argument("--no-solve", action="store_true", help="skip both time-to-solution legs")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the heavy multishift and uneven batch workloads")
+    ap.add_argument("--ptc", action="store_true",
+                    help="also train the PTC preconditioner on 48^3x96 and time PTC-FCG (several minutes)")
+    ap.add_argument("--ptc-pairs", type=int, default=2048)
+    ap.add_argument("--ptc-configs", type=int, default=8)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -13,7 +13,7 @@
 // it filled itself, so the pipeline needs no block barrier (cp.async.wait_group
 // makes a thread's own copies visible to it).
 //
-// Shared memory per thread (16-bit, light): odd pass 548 B, even pass 640 B.
+// Shared memory per thread (16-bit, light, 12-real links): odd pass 500 B, even pass 592 B.
 #include "tm_internal.h"
 #include "tm_kernels.h"
 #include "dslash_common.cuh"
@@ -53,7 +53,8 @@ struct Stg {
     static constexpr int LOC = (KIND == K2_OE_LOCAL) ? 1 : 0;
     static constexpr int U16 = 4 * SP16 + CLV16 + LOC * SP16;           // 16-B units per thread
     static constexpr int NN = NORM ? (4 + LOC) : 0;                     // FP32 scales per thread
-    static constexpr int BYTES = U16 * 16 + 36 * LB + NN * 4;           // shared bytes per thread
+    static constexpr int NL = LinkStore<P>::N;                          // stored complex per link
+    static constexpr int BYTES = U16 * 16 + 4 * NL * LB + NN * 4;       // shared bytes per thread
 };
 
 template <int P, int NC>
@@ -114,8 +115,9 @@ __device__ __forceinline__ void reals_from_smem(const uint4* s16, int unit0, int
 template <int P>
 __device__ __forceinline__ void link_from_smem(const unsigned char* sL, int unit0, int BS, int t,
                                                cpx<typename PT<P>::R>* u) {
+    constexpr int N = LinkStore<P>::N;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < N; ++k) {
         const int e = (unit0 + k) * BS + t;
         if constexpr (P == P64) {
             const double2 q = reinterpret_cast<const double2*>(sL)[e];
@@ -128,6 +130,7 @@ __device__ __forceinline__ void link_from_smem(const unsigned char* sL, int unit
             u[k] = C(h2f<P>((uint16_t)(q & 0xffffu)), h2f<P>((uint16_t)(q >> 16)));
         }
     }
+    if constexpr (N == 6) su3_third_row(u);
 }
 
 template <int P, int NF, int KIND, int NP, int BS>
@@ -138,7 +141,7 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
     extern __shared__ __align__(16) unsigned char smem[];
     uint4* s16 = reinterpret_cast<uint4*>(smem);
     unsigned char* sL = smem + (size_t)G::U16 * BS * 16;
-    float* sN = reinterpret_cast<float*>(sL + (size_t)36 * BS * G::LB);
+    float* sN = reinterpret_cast<float*>(sL + (size_t)4 * G::NL * BS * G::LB);
     __shared__ double shred[BS / 32];
 
     const int k = find_problem<NP>(b, blockIdx.x);
@@ -173,8 +176,8 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
         auto issue_link = [&](const void* base, int mu, long idx, int unit0) {
             const unsigned char* gp = reinterpret_cast<const unsigned char*>(base);
 #pragma unroll
-            for (int kk = 0; kk < 9; ++kk) {
-                const unsigned char* src = gp + ((long)(mu * 9 + kk) * g.vh + idx) * G::LB;
+            for (int kk = 0; kk < G::NL; ++kk) {
+                const unsigned char* src = gp + ((long)(mu * G::NL + kk) * g.vh + idx) * G::LB;
                 unsigned char* dst = sL + (size_t)((unit0 + kk) * BS + t) * G::LB;
                 if constexpr (G::LB == 16) cp_async16(dst, src);
                 else if constexpr (G::LB == 8) cp_async8(dst, src);
@@ -185,9 +188,9 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
             long nf, nb;
             nbr(mu, nf, nb);
             issue_spinor(pr.in, nf, (buf * 2 + 0) * G::SP16, buf * 2 + 0);
-            issue_link(pr.gauge[po], mu, i, (buf * 2 + 0) * 9);
+            issue_link(pr.gauge[po], mu, i, (buf * 2 + 0) * G::NL);
             issue_spinor(pr.in, nb, (buf * 2 + 1) * G::SP16, buf * 2 + 1);
-            issue_link(pr.gauge[1 - po], mu, nb, (buf * 2 + 1) * 9);
+            issue_link(pr.gauge[1 - po], mu, nb, (buf * 2 + 1) * G::NL);
         };
         // group 0: site-local epilogue data; groups 1, 2: directions 0, 1
         {
@@ -217,11 +220,11 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
             cpx<R> u[9];
             cpx<R> psi[NC];
             sp_from_smem<P, NC>(s16, (buf * 2 + 0) * G::SP16, sN, buf * 2 + 0, BS, t, psi);
-            link_from_smem<P>(sL, (buf * 2 + 0) * 9, BS, t, u);
+            link_from_smem<P>(sL, (buf * 2 + 0) * G::NL, BS, t, u);
 #pragma unroll
             for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false>(acc[f], psi + 12 * f, u, MU == 3 ? phf : (R)1);
             sp_from_smem<P, NC>(s16, (buf * 2 + 1) * G::SP16, sN, buf * 2 + 1, BS, t, psi);
-            link_from_smem<P>(sL, (buf * 2 + 1) * 9, BS, t, u);
+            link_from_smem<P>(sL, (buf * 2 + 1) * G::NL, BS, t, u);
 #pragma unroll
             for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true>(acc[f], psi + 12 * f, u, MU == 3 ? phb : (R)1);
         };

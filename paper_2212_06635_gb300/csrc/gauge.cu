@@ -28,12 +28,16 @@ __global__ void k_gauge_import(void* dst0, void* dst1, const double* __restrict_
     for (int k = 0; k < 9; ++k) d[(long)(mu * 9 + k) * g.vh + cb] = s[k];
 }
 
-// native FP64 links of one parity -> native precision P (36 complex per site)
+// native FP64 links of one parity (9 complex per direction) -> native precision P
+// (the first LinkStore<P>::N complex per direction; FP32/16-bit keep rows 0, 1)
 template <int P>
 __global__ void k_links_from64(void* dst, const double2* __restrict__ src, long vh) {
-    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 36 * vh) return;
-    const double2 v = src[e];
+    constexpr int N = LinkStore<P>::N;
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;   // destination element
+    if (e >= 4 * N * vh) return;
+    const long w = e / vh, i = e - w * vh;
+    const int mu = (int)(w / N), k = (int)(w % N);
+    const double2 v = src[(long)(mu * 9 + k) * vh + i];
     if constexpr (P == P32) {
         reinterpret_cast<float2*>(dst)[e] = make_float2((float)v.x, (float)v.y);
     } else if constexpr (P == P64) {
@@ -316,7 +320,7 @@ cudaError_t launch_gauge_import(void* d0, void* d1, const double* src, const Geo
 
 template <int P>
 cudaError_t launch_links_from64(void* dst, const void* src64, long vh, cudaStream_t st) {
-    const long n = 36 * vh;
+    const long n = 4 * LinkStore<P>::N * vh;
     k_links_from64<P><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(dst, reinterpret_cast<const double2*>(src64), vh);
     return cudaGetLastError();
 }

@@ -72,8 +72,9 @@ __host__ __device__ inline size_t spinor_bytes(int p, int nc, long vh) {
     if (p == PB16 || p == PF16) b += (size_t)vh * sizeof(float);
     return b;
 }
+// FP64 links store 18 reals, FP32 / 16-bit links 12 (two rows; see load_link)
 __host__ __device__ inline size_t link_bytes_parity(int p, long vh) {
-    return (size_t)vh * 4 * 18 * prec_esz(p);
+    return (size_t)vh * 4 * (p == P64 ? 18 : 12) * prec_esz(p);
 }
 
 template <int P> __device__ __forceinline__ float h2f(uint16_t v);
@@ -168,13 +169,28 @@ __device__ __forceinline__ void store_spinor(void* base, long vh, long i,
     }
 }
 
-// SU(3) link (9 complex, row major) of direction mu at site i of one parity.
+// Complex entries stored per link: FP64 keeps all 9 (its passes are bound by
+// FP64 arithmetic, not bytes); FP32 and 16-bit keep the first two rows only (12
+// reals) and rebuild the third from unitarity with det U = 1.
+template <int P> struct LinkStore { static constexpr int N = (P == P64) ? 9 : 6; };
+
+// row 2 of an SU(3) matrix = conj(row 0 x row 1)
+template <typename R>
+__device__ __forceinline__ void su3_third_row(cpx<R>* u) {
+    u[6] = cj(u[1] * u[5] - u[2] * u[4]);
+    u[7] = cj(u[2] * u[3] - u[0] * u[5]);
+    u[8] = cj(u[0] * u[4] - u[1] * u[3]);
+}
+
+// SU(3) link (9 complex, row major) of direction mu at site i of one parity;
+// element k of direction mu lives at (mu * LinkStore<P>::N + k) * vh + i.
 template <int P>
 __device__ __forceinline__ void load_link(const void* base, long vh, int mu, long i,
                                           cpx<typename PT<P>::R>* u) {
+    constexpr int N = LinkStore<P>::N;
 #pragma unroll
-    for (int k = 0; k < 9; ++k) {
-        const long e = (long)(mu * 9 + k) * vh + i;
+    for (int k = 0; k < N; ++k) {
+        const long e = (long)(mu * N + k) * vh + i;
         if constexpr (P == P64) {
             double2 q = __ldg(reinterpret_cast<const double2*>(base) + e);
             u[k] = C(q.x, q.y);
@@ -186,6 +202,7 @@ __device__ __forceinline__ void load_link(const void* base, long vh, int mu, lon
             u[k] = C(h2f<P>((uint16_t)(q & 0xffffu)), h2f<P>((uint16_t)(q >> 16)));
         }
     }
+    if constexpr (N == 6) su3_third_row(u);
 }
 
 // ---------------------------------------------------------------------------

@@ -28,6 +28,8 @@ def main():
     ap.add_argument("--prec", default="f16", choices=list(PRECS))
     ap.add_argument("--heavy", action="store_true")
     ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--variant", default="direct", choices=["direct", "staged", "auto"],
+                    help="stencil kernel variant of both passes (auto = tm_autotune)")
     a = ap.parse_args()
     import torch
     from paper_2212_06635_gb300 import tm
@@ -46,11 +48,17 @@ def main():
         f = torch.empty(tm.tm_field_bytes(ctx, prec, nf), dtype=torch.uint8, device="cuda")
         tm.tm_field_import(ctx, prec, nf, f, bd)
         op = tm.TM_QH if a.heavy else tm.TM_QHAT_PLUS
+        if a.variant == "auto":
+            tm.tm_autotune(ctx, prec, nf)
+        elif prec != 0:
+            v = 1 if a.variant == "staged" else 0
+            tm.tm_set_tuning(ctx, prec, nf, v, v)
         t1, t2 = tm.tm_kernel_times(ctx, op, prec, f, a.reps)
         vh = int(np.prod(dims)) // 2
         esz = ESZ[prec]
         sc = 4 if prec >= 2 else 0
-        r1, r2 = (384, 360) if a.heavy else (336, 288)
+        links = 8 * (18 if prec == 0 else 12)
+        r1, r2 = (links + 240, links + 216) if a.heavy else (links + 192, links + 144)
         s1, s2 = (2, 3)
         b1 = (r1 * esz + s1 * sc) * vh
         b2 = (r2 * esz + s2 * sc) * vh
