@@ -45,11 +45,11 @@ def mhat_bytes_per_site(prec):
     """Algorithmic bytes of one M_hat application per odd site (each field read or
     written once per pass): even pass 8 links + psi 24 + inverse blocks 144 +
     t_e 24 reals, odd pass 8 links + t_e 24 + psi 24 + clover 72 + out 24 reals.
-    A link is 18 reals in FP64 and 12 (two rows) in FP32 / 16-bit storage; 16-bit
+    A link is 12 reals (two rows) in FP32 and FP16 storage and 18 in FP64 and BF16; 16-bit
     spinors add one FP32 scale per site per spinor access."""
     esz = ESZ[prec]
     scale = 4 if prec in (2, 3) else 0
-    links = 8 * (18 if prec == 0 else 12)
+    links = 8 * (12 if prec in (1, 3) else 18)
     k1 = (links + 192) * esz + 2 * scale
     k2 = (links + 144) * esz + 3 * scale
     return k1, k2

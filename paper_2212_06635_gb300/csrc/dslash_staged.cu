@@ -76,8 +76,9 @@ __device__ __forceinline__ void sp_from_smem(const uint4* s16, int unit0, const 
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                r[8 * u + 2 * k] = h2f<P>((uint16_t)(w[k] & 0xffffu));
-                r[8 * u + 2 * k + 1] = h2f<P>((uint16_t)(w[k] >> 16));
+                const float2 f = h2f2<P>(w[k]);
+                r[8 * u + 2 * k] = f.x;
+                r[8 * u + 2 * k + 1] = f.y;
             }
         }
     }
@@ -105,8 +106,9 @@ __device__ __forceinline__ void reals_from_smem(const uint4* s16, int unit0, int
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                r[8 * u + 2 * k] = h2f<P>((uint16_t)(w[k] & 0xffffu));
-                r[8 * u + 2 * k + 1] = h2f<P>((uint16_t)(w[k] >> 16));
+                const float2 f = h2f2<P>(w[k]);
+                r[8 * u + 2 * k] = f.x;
+                r[8 * u + 2 * k + 1] = f.y;
             }
         }
     }
@@ -127,7 +129,8 @@ __device__ __forceinline__ void link_from_smem(const unsigned char* sL, int unit
             u[k] = C(q.x, q.y);
         } else {
             const uint32_t q = reinterpret_cast<const uint32_t*>(sL)[e];
-            u[k] = C(h2f<P>((uint16_t)(q & 0xffffu)), h2f<P>((uint16_t)(q >> 16)));
+            const float2 f = h2f2<P>(q);
+            u[k] = C(f.x, f.y);
         }
     }
     if constexpr (N == 6) su3_third_row(u);

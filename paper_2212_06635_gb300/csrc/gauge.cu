@@ -43,7 +43,7 @@ __global__ void k_links_from64(void* dst, const double2* __restrict__ src, long 
     } else if constexpr (P == P64) {
         reinterpret_cast<double2*>(dst)[e] = v;
     } else {
-        const uint32_t w = (uint32_t)f2h<P>((float)v.x) | ((uint32_t)f2h<P>((float)v.y) << 16);
+        const uint32_t w = f2h2<P>((float)v.x, (float)v.y);
         reinterpret_cast<unsigned int*>(dst)[e] = w;
     }
 }

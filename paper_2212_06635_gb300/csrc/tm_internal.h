@@ -72,9 +72,9 @@ __host__ __device__ inline size_t spinor_bytes(int p, int nc, long vh) {
     if (p == PB16 || p == PF16) b += (size_t)vh * sizeof(float);
     return b;
 }
-// FP64 links store 18 reals, FP32 / 16-bit links 12 (two rows; see load_link)
+// FP64 and BF16 links store 18 reals, FP32 / FP16 links 12 (two rows; see load_link)
 __host__ __device__ inline size_t link_bytes_parity(int p, long vh) {
-    return (size_t)vh * 4 * (p == P64 ? 18 : 12) * prec_esz(p);
+    return (size_t)vh * 4 * ((p == P32 || p == PF16) ? 12 : 18) * prec_esz(p);
 }
 
 template <int P> __device__ __forceinline__ float h2f(uint16_t v);
@@ -83,6 +83,31 @@ template <> __device__ __forceinline__ float h2f<PB16>(uint16_t v) { return __bf
 template <int P> __device__ __forceinline__ uint16_t f2h(float v);
 template <> __device__ __forceinline__ uint16_t f2h<PF16>(float v) { return __half_as_ushort(__float2half_rn(v)); }
 template <> __device__ __forceinline__ uint16_t f2h<PB16>(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
+
+// paired conversions of a 32-bit word holding two 16-bit values (low half first)
+template <int P> __device__ __forceinline__ float2 h2f2(uint32_t w);
+template <> __device__ __forceinline__ float2 h2f2<PF16>(uint32_t w) {
+    __half2 h;
+    memcpy(&h, &w, 4);
+    return __half22float2(h);
+}
+template <> __device__ __forceinline__ float2 h2f2<PB16>(uint32_t w) {
+    // a BF16 value is the upper 16 bits of the FP32 value
+    return make_float2(__uint_as_float(w << 16), __uint_as_float(w & 0xffff0000u));
+}
+template <int P> __device__ __forceinline__ uint32_t f2h2(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t f2h2<PF16>(float lo, float hi) {
+    const __half2 h = __floats2half2_rn(lo, hi);
+    uint32_t w;
+    memcpy(&w, &h, 4);
+    return w;
+}
+template <> __device__ __forceinline__ uint32_t f2h2<PB16>(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    uint32_t w;
+    memcpy(&w, &h, 4);
+    return w;
+}
 
 // Load NR reals (NR multiple of W) starting at real offset OFF of site i.
 template <int P, int NR>
@@ -104,8 +129,9 @@ __device__ __forceinline__ void load_reals(const void* base, long vh, long i, in
             const uint32_t w[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                dst[8 * v + 2 * k] = h2f<P>((uint16_t)(w[k] & 0xffffu));
-                dst[8 * v + 2 * k + 1] = h2f<P>((uint16_t)(w[k] >> 16));
+                const float2 f = h2f2<P>(w[k]);
+                dst[8 * v + 2 * k] = f.x;
+                dst[8 * v + 2 * k + 1] = f.y;
             }
         }
     }
@@ -128,7 +154,7 @@ __device__ __forceinline__ void store_reals(void* base, long vh, long i, int off
             uint32_t w[4];
 #pragma unroll
             for (int k = 0; k < 4; ++k)
-                w[k] = (uint32_t)f2h<P>(src[8 * v + 2 * k]) | ((uint32_t)f2h<P>(src[8 * v + 2 * k + 1]) << 16);
+                w[k] = f2h2<P>(src[8 * v + 2 * k], src[8 * v + 2 * k + 1]);
             reinterpret_cast<uint4*>(base)[e] = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
@@ -169,10 +195,12 @@ __device__ __forceinline__ void store_spinor(void* base, long vh, long i,
     }
 }
 
-// Complex entries stored per link: FP64 keeps all 9 (its passes are bound by
-// FP64 arithmetic, not bytes); FP32 and 16-bit keep the first two rows only (12
-// reals) and rebuild the third from unitarity with det U = 1.
-template <int P> struct LinkStore { static constexpr int N = (P == P64) ? 9 : 6; };
+// Complex entries stored per link: FP32 and FP16 keep the first two rows only (12
+// reals) and rebuild the third from unitarity with det U = 1.  FP64 keeps all 9
+// (its passes are bound by FP64 arithmetic, not bytes), and so does BF16: a third
+// row rebuilt from two rows rounded to BF16's 8-bit significand exceeds the 3e-3
+// operator error budget.
+template <int P> struct LinkStore { static constexpr int N = (P == P32 || P == PF16) ? 6 : 9; };
 
 // row 2 of an SU(3) matrix = conj(row 0 x row 1)
 template <typename R>
@@ -199,7 +227,8 @@ __device__ __forceinline__ void load_link(const void* base, long vh, int mu, lon
             u[k] = C(q.x, q.y);
         } else {
             uint32_t q = __ldg(reinterpret_cast<const unsigned int*>(base) + e);
-            u[k] = C(h2f<P>((uint16_t)(q & 0xffffu)), h2f<P>((uint16_t)(q >> 16)));
+            const float2 f = h2f2<P>(q);
+            u[k] = C(f.x, f.y);
         }
     }
     if constexpr (N == 6) su3_third_row(u);

@@ -57,7 +57,7 @@ def main():
         vh = int(np.prod(dims)) // 2
         esz = ESZ[prec]
         sc = 4 if prec >= 2 else 0
-        links = 8 * (18 if prec == 0 else 12)
+        links = 8 * (12 if prec in (1, 3) else 18)
         r1, r2 = (links + 240, links + 216) if a.heavy else (links + 192, links + 144)
         s1, s2 = (2, 3)
         b1 = (r1 * esz + s1 * sc) * vh
