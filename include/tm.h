@@ -70,7 +70,10 @@ typedef enum {
     TM_QPQM = 3,         /* Q_hat_+ Q_hat_-  (HMC ordering, HPD)               light */
     TM_QH = 4,           /* Q_hat_h  (eq:hQh)                                   heavy */
     TM_QH_DAG = 5,       /* Q_hat_h^dagger = tau1 Q_hat_h tau1 (mubar -> -mubar) heavy */
-    TM_QH_SQ = 6         /* Q_hat_h Q_hat_h^dagger  (HPD)                       heavy */
+    TM_QH_SQ = 6,        /* Q_hat_h Q_hat_h^dagger  (HPD)                       heavy */
+    TM_WHAT_PLUS = 7,    /* W_hat_+(rho) = Q_hat_+ + i rho (eq:hWpm)            light */
+    TM_WHAT_MINUS = 8,   /* W_hat_-(rho) = Q_hat_- - i rho = W_hat_+^dagger     light */
+    TM_WHAT_SQ = 9       /* W_hat_- W_hat_+ = W_hat_+^dagger W_hat_+  (HPD)     light */
 } tm_op;
 
 typedef struct {
@@ -79,6 +82,9 @@ typedef struct {
     double mubar;       /* heavy doublet mu_sigma (eq:hQh) */
     double epsbar;      /* heavy doublet mu_delta (eq:hQh) */
     int bc_t;           /* +1 periodic, -1 antiperiodic in time */
+    double rho;         /* mass-preconditioning mass of W_hat (eq:hWpm); enters as
+                           i 2 kappa rho on odd sites and leaves the clover inverse
+                           rho-independent, as Sec. 2 notes */
 } tm_params;
 
 typedef struct {
@@ -159,7 +165,7 @@ tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, 
 tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,
                         void* stream);
 
-/* Solve A x = b, A = TM_MDAGM, TM_QPQM or TM_QH_SQ, by CG (sloppy = TM_F64) or by
+/* Solve A x = b, A = TM_MDAGM, TM_QPQM, TM_QH_SQ or TM_WHAT_SQ, by CG (sloppy = TM_F64) or by
  * mixed-precision CG with reliable updates (Sec. 4.1).  x, b canonical FP64, host
  * or device pointers; x is the initial guess on entry (zero it for none). */
 tm_status tm_solve_cg(tm_ctx* ctx, tm_op op, const tm_solve_params* sp, double* x,

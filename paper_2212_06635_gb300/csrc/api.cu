@@ -59,7 +59,8 @@ extern "C" const char* tm_last_error(void) { return g_err; }
 // ---------------------------------------------------------------------------
 static inline cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
 static inline int nblk(long vh, int bs) { return (int)((vh + bs - 1) / bs); }
-static inline int nflav(tm_op op) { return op >= TM_QH ? 2 : 1; }
+static inline int nflav(tm_op op) { return (op == TM_QH || op == TM_QH_DAG || op == TM_QH_SQ) ? 2 : 1; }
+static inline bool is_what(tm_op op) { return op == TM_WHAT_PLUS || op == TM_WHAT_MINUS || op == TM_WHAT_SQ; }
 
 static bool is_device_ptr(const void* p) {
     cudaPointerAttributes a;
@@ -182,6 +183,7 @@ extern "C" tm_status tm_gauge_id(const tm_ctx* c, double* id) {
     return TM_OK;
 }
 
+// parameters the clover term and its inverses depend on (rho does not enter them)
 static bool same_params(const tm_params& a, const tm_params& b) {
     return a.kappa == b.kappa && a.csw == b.csw && a.mu == b.mu && a.mubar == b.mubar &&
            a.epsbar == b.epsbar && a.bc_t == b.bc_t;
@@ -193,7 +195,10 @@ extern "C" tm_status tm_clover_compute(tm_ctx* c, const tm_params* prm, void* st
     if (prm->bc_t != 1 && prm->bc_t != -1) return fail(TM_ERR_ARG, "tm_clover_compute: bc_t must be +1 or -1");
     if (!(prm->kappa > 0.0)) return fail(TM_ERR_ARG, "tm_clover_compute: kappa must be positive");
     CK(cudaSetDevice(c->device));
-    if (c->clover_gauge_gen == c->gauge_gen && same_params(c->params, *prm)) return TM_OK;
+    if (c->clover_gauge_gen == c->gauge_gen && same_params(c->params, *prm)) {
+        c->params.rho = prm->rho;   // W_hat's rho leaves the clover inverse unchanged (Sec. 2)
+        return TM_OK;
+    }
     const cudaStream_t st = S(stream);
     const long vh = c->vh;
     const bool heavy = prm->mubar != 0.0 || prm->epsbar != 0.0;
@@ -289,7 +294,7 @@ static cudaError_t launch_pass(int variant, const OpBatch<NP>& b, int nb, cudaSt
 }
 
 static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void* out, const void* in,
-                        const void* loc, SolverCtl* ctl, bool fuse) {
+                        const void* loc, SolverCtl* ctl, bool fuse, double rho = 0.0) {
     OpProb p{};
     p.g = c->g;
     p.nblk = nblk(c->vh, pass_bs(c, P, nf, kind));
@@ -304,6 +309,7 @@ static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void
     p.kappa = k;
     p.tw = sign * 2.0 * k * (nf == 1 ? c->params.mu : c->params.mubar);
     p.eps = 2.0 * k * c->params.epsbar;
+    p.rho = kind == K2_OE_LOCAL ? rho : 0.0;
     p.sign = sign;
     p.ctl = ctl;
     p.ms = c->ms;
@@ -312,10 +318,11 @@ static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void
     return p;
 }
 
-// out = Q_hat(sign) in, via the even temporary te.  fin != FIN_NONE fuses ||out||^2.
+// out = Q_hat(sign) in (+ i rho in for W_hat), via the even temporary te.
+// fin != FIN_NONE fuses ||out||^2.
 template <int P, int NF>
 static cudaError_t schur(const tm_ctx* c, int sign, void* out, const void* in, void* te, cudaStream_t st,
-                         SolverCtl* ctl, int fin) {
+                         SolverCtl* ctl, int fin, double rho = 0.0) {
     OpBatch<1> b{};
     b.n = 1;
     b.fin = FIN_NONE;
@@ -325,14 +332,14 @@ static cudaError_t schur(const tm_ctx* c, int sign, void* out, const void* in, v
     cudaError_t e = launch_pass<P, NF, K1_EO_INV, 1>(c->variant[P][NF - 1][K1_EO_INV], b, b.p[0].nblk, st);
     if (e != cudaSuccess) return e;
     b.fin = fin;
-    b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, ctl, fin != FIN_NONE);
+    b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, ctl, fin != FIN_NONE, rho);
     b.blk_start[1] = b.p[0].nblk;
     return launch_pass<P, NF, K2_OE_LOCAL, 1>(c->variant[P][NF - 1][K2_OE_LOCAL], b, b.p[0].nblk, st);
 }
 
 // signs of the two factors of a normal operator (first applied first)
 static void normal_signs(tm_op op, int* s1, int* s2) {
-    if (op == TM_MDAGM) { *s1 = +1; *s2 = -1; }        // Q- Q+
+    if (op == TM_MDAGM || op == TM_WHAT_SQ) { *s1 = +1; *s2 = -1; }   // Q- Q+, W- W+
     else if (op == TM_QPQM) { *s1 = -1; *s2 = +1; }    // Q+ Q-
     else { *s1 = -1; *s2 = +1; }                       // Qh Qh^+
 }
@@ -343,9 +350,10 @@ static cudaError_t normal_op(const tm_ctx* c, tm_op op, void* out, const void* i
                              cudaStream_t st, SolverCtl* ctl, int fin) {
     int s1, s2;
     normal_signs(op, &s1, &s2);
-    cudaError_t e = schur<P, NF>(c, s1, mid, in, te, st, ctl, fin);
+    const double rt = is_what(op) ? 2.0 * c->params.kappa * c->params.rho : 0.0;
+    cudaError_t e = schur<P, NF>(c, s1, mid, in, te, st, ctl, fin, s1 * rt);
     if (e != cudaSuccess) return e;
-    return schur<P, NF>(c, s2, out, mid, te, st, ctl, FIN_NONE);
+    return schur<P, NF>(c, s2, out, mid, te, st, ctl, FIN_NONE, s2 * rt);
 }
 
 template <int P, int NF>
@@ -356,6 +364,9 @@ static tm_status apply_t(tm_ctx* c, tm_op op, void* out, const void* in, cudaStr
         CK(schur<P, NF>(c, +1, out, in, te, st, nullptr, FIN_NONE));
     } else if (op == TM_QHAT_MINUS || op == TM_QH_DAG) {
         CK(schur<P, NF>(c, -1, out, in, te, st, nullptr, FIN_NONE));
+    } else if (op == TM_WHAT_PLUS || op == TM_WHAT_MINUS) {
+        const int sg = op == TM_WHAT_PLUS ? +1 : -1;
+        CK(schur<P, NF>(c, sg, out, in, te, st, nullptr, FIN_NONE, sg * 2.0 * c->params.kappa * c->params.rho));
     } else {
         CKS(ws_get(c, WS_APPLY_MID, spinor_bytes(P, 12 * NF, c->vh), &mid));
         CK(normal_op<P, NF>(c, op, out, in, mid, te, st, nullptr, FIN_NONE));
@@ -371,7 +382,7 @@ static tm_status check_prec(int p) {
 extern "C" tm_status tm_apply_Mhat(tm_ctx* c, tm_op op, tm_prec prec, void* out, const void* in, void* stream) {
     if (!c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_apply_Mhat: bad pointers");
     if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_Mhat: fields must be 16-byte aligned");
-    if (op < TM_QHAT_PLUS || op > TM_QH_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown op %d", (int)op);
+    if (op < TM_QHAT_PLUS || op > TM_WHAT_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown op %d", (int)op);
     CKS(check_prec(prec));
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
@@ -889,8 +900,8 @@ static tm_status enter_solver(tm_ctx* c, void* stream) {
 }
 
 static tm_status check_solver_op(tm_ctx* c, tm_op op) {
-    if (op != TM_MDAGM && op != TM_QPQM && op != TM_QH_SQ)
-        return fail(TM_ERR_ARG, "solver op must be TM_MDAGM, TM_QPQM or TM_QH_SQ");
+    if (op != TM_MDAGM && op != TM_QPQM && op != TM_QH_SQ && op != TM_WHAT_SQ)
+        return fail(TM_ERR_ARG, "solver op must be TM_MDAGM, TM_QPQM, TM_QH_SQ or TM_WHAT_SQ");
     if (op == TM_QH_SQ && !c->have_heavy)
         return fail(TM_ERR_ARG, "heavy operator needs mubar or epsbar in tm_clover_compute");
     return TM_OK;

@@ -308,6 +308,11 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
                     for (int j = 0; j < 6; ++j) out[12 * f + 6 * cb + j] = (cb == 0) ? w[j] : -w[j];
                 }
             }
+            if (pr.rho != 0.0) {   // W_hat = Q_hat + i rho (eq:hWpm)
+                const R rh = (R)pr.rho;
+#pragma unroll
+                for (int q = 0; q < NC; ++q) out[q] = out[q] + rh * mul_i(psi[q]);
+            }
             if (pr.partial != nullptr) {
                 R s = (R)0;
 #pragma unroll

@@ -309,6 +309,7 @@ struct OpProb {
     double kappa;
     double tw;               // light: sign*mu_t; heavy: sign*mubar_t (K2 local term)
     double eps;              // heavy: epsbar_t
+    double rho;              // odd pass: out += i rho psi (W_hat: sign * 2 kappa rho; else 0)
     int sign;                // +1 / -1 (which inverse / adjoint)
     SolverCtl* ctl;          // early exit when ctl->flag != 0 (may be null)
     MsCtl* ms;               // multishift state for FIN_MS_ALPHA (may be null)

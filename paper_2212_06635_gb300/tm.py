@@ -19,7 +19,8 @@ LIB_PATH = os.path.join(_HERE, "libtm.so")
 TM_OK, TM_ERR_ARG, TM_ERR_CUDA, TM_ERR_OOM, TM_ERR_STALE, TM_ERR_NOT_CONVERGED, \
     TM_ERR_BREAKDOWN, TM_ERR_TIMEOUT, TM_ERR_UNSUPPORTED = range(9)
 TM_F64, TM_F32, TM_BF16, TM_F16 = range(4)
-TM_QHAT_PLUS, TM_QHAT_MINUS, TM_MDAGM, TM_QPQM, TM_QH, TM_QH_DAG, TM_QH_SQ = range(7)
+TM_QHAT_PLUS, TM_QHAT_MINUS, TM_MDAGM, TM_QPQM, TM_QH, TM_QH_DAG, TM_QH_SQ, TM_WHAT_PLUS, TM_WHAT_MINUS, \
+    TM_WHAT_SQ = range(10)
 
 PREC_NAMES = {TM_F64: "f64", TM_F32: "f32", TM_BF16: "bf16", TM_F16: "f16"}
 STATUS_NAMES = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_CUDA", 3: "TM_ERR_OOM", 4: "TM_ERR_STALE",
@@ -29,7 +30,7 @@ STATUS_NAMES = {0: "TM_OK", 1: "TM_ERR_ARG", 2: "TM_ERR_CUDA", 3: "TM_ERR_OOM", 
 
 class tm_params(ct.Structure):
     _fields_ = [("kappa", ct.c_double), ("csw", ct.c_double), ("mu", ct.c_double),
-                ("mubar", ct.c_double), ("epsbar", ct.c_double), ("bc_t", ct.c_int)]
+                ("mubar", ct.c_double), ("epsbar", ct.c_double), ("bc_t", ct.c_int), ("rho", ct.c_double)]
 
 
 class tm_solve_params(ct.Structure):
@@ -168,8 +169,8 @@ def tm_gauge_id(ctx):
     return v.value
 
 
-def tm_clover_compute(ctx, kappa, csw, mu=0.0, mubar=0.0, epsbar=0.0, bc_t=-1, stream=None):
-    p = tm_params(kappa, csw, mu, mubar, epsbar, int(bc_t))
+def tm_clover_compute(ctx, kappa, csw, mu=0.0, mubar=0.0, epsbar=0.0, bc_t=-1, rho=0.0, stream=None):
+    p = tm_params(kappa, csw, mu, mubar, epsbar, int(bc_t), float(rho))
     _check(lib.tm_clover_compute(ctx, ct.byref(p), _stream(stream)))
 
 

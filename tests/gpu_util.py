@@ -32,14 +32,14 @@ def rel(a, b):
 class Lat:
     """A context with a gauge field and clover term loaded."""
 
-    def __init__(self, u, dims, kappa, csw, mu=0.0, mubar=0.0, epsbar=0.0, bc_t=-1, gauge_id=1.0):
+    def __init__(self, u, dims, kappa, csw, mu=0.0, mubar=0.0, epsbar=0.0, bc_t=-1, gauge_id=1.0, rho=0.0):
         from paper_2212_06635_gb300 import tm
         self.tm = tm
         self.dims = dims
         self.vh = int(np.prod(dims)) // 2
         self.ctx = tm.tm_create(dims, 0)
         tm.tm_gauge_load(self.ctx, np.ascontiguousarray(u), gauge_id)
-        tm.tm_clover_compute(self.ctx, kappa, csw, mu=mu, mubar=mubar, epsbar=epsbar, bc_t=bc_t)
+        tm.tm_clover_compute(self.ctx, kappa, csw, mu=mu, mubar=mubar, epsbar=epsbar, bc_t=bc_t, rho=rho)
 
     def close(self):
         if self.ctx:

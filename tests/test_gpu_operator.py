@@ -123,3 +123,26 @@ def test_autotune_choice_is_kept():
             tm.tm_set_tuning(lat.ctx, tm.TM_F64, 1, 1, 1)
     finally:
         lat.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3], ids=["f64", "f32", "f16"])
+def test_mass_preconditioned_W_hat(prec):
+    """W_hat_pm(rho) = Q_hat_pm pm i rho (eq:hWpm) and W_hat_- W_hat_+; changing rho
+    leaves the clover term untouched (it is rho-independent, Sec. 2)."""
+    dims = (6, 4, 4, 6)
+    u = F.gauge_field(dims, 71)
+    op = D.TwistedMassClover(u, dims, KAPPA, CSW, mu=MU)
+    lat = Lat(u, dims, KAPPA, CSW, mu=MU)
+    try:
+        tm = lat.tm
+        psi = F.odd_spinor(dims, 72)
+        for rho in (0.05, 0.3):
+            tm.tm_clover_compute(lat.ctx, KAPPA, CSW, mu=MU, rho=rho)
+            wp = op.What(psi, rho, +1)
+            wm = op.What(psi, rho, -1)
+            wsq = op.What(op.What(psi, rho, +1), rho, -1)
+            assert rel(lat.apply(tm.TM_WHAT_PLUS, prec, psi), wp) < tol(prec)
+            assert rel(lat.apply(tm.TM_WHAT_MINUS, prec, psi), wm) < tol(prec)
+            assert rel(lat.apply(tm.TM_WHAT_SQ, prec, psi), wsq) < tol(prec, 2)
+    finally:
+        lat.close()

@@ -227,3 +227,19 @@ def test_solvers_with_staged_kernels():
         assert S.rel_residual(op.MdagM, from_dev(x, b.shape), b) <= 1.05e-10
     finally:
         lat.close()
+
+
+def test_cg_on_W_hat_normal_operator():
+    dims = (6, 4, 4, 6)
+    u = F.gauge_field(dims, 1900)
+    op = D.TwistedMassClover(u, dims, 0.14, CSW, mu=0.004)
+    lat = Lat(u, dims, 0.14, CSW, mu=0.004, rho=0.1)
+    tm = lat.tm
+    try:
+        b = F.odd_spinor(dims, 1901)
+        x = to_dev(np.zeros_like(b))
+        tm.tm_solve_cg(lat.ctx, tm.TM_WHAT_SQ, tm.solve_params(tol=1e-10, sloppy=tm.TM_F16), x, to_dev(b))
+        A = lambda v: op.What(op.What(v, 0.1, +1), 0.1, -1)
+        assert S.rel_residual(A, from_dev(x, b.shape), b) <= 1.05e-10
+    finally:
+        lat.close()
