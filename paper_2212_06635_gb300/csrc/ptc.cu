@@ -82,34 +82,50 @@ __device__ __forceinline__ void act_load(const uint4* a, long V, int b, long y, 
     }
 }
 
-// (T_p in^b)(x): 12 complex
-__device__ __forceinline__ void transported(const PtcGeom& g, const uint4* in, int b, long x, int p,
-                                            cpx<float> (&w)[12]) {
-    if (p == 0) {
-        act_load(in, g.V, b, x, w);
-        return;
-    }
-    cpx<float> u[9], v[12];
-    bool dag;
-    float ph;
-    const long y = path_site(g, x, p, u, dag, ph);
-    act_load(in, g.V, b, y, v);
+// Transport channels [b0, b0 + n) of `in` along path p to site x: the link and
+// the neighbour index are computed once for the whole channel group; each
+// transported 12-complex (spin, colour) spinor is handed to sink(b, w).
+template <int NMAX, typename Sink>
+__device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4* in, long x, int p, int b0,
+                                                   int n, Sink&& sink) {
+    cpx<float> u[9];
+    bool dag = false;
+    float ph = 1.f;
+    long y = x;
+    if (p != 0) y = path_site(g, x, p, u, dag, ph);
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
+    for (int k = 0; k < NMAX; ++k) {
+        if (k >= n) break;
+        const int b = b0 + k;
+        cpx<float> v[12], w[12];
+        act_load(in, g.V, b, y, v);
+        if (p == 0) {
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            cpx<float> t = C(0.f, 0.f);
+            for (int q = 0; q < 12; ++q) w[q] = v[q];
+        } else {
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                if (dag) cfma_cj(t, u[3 * d + c], v[3 * s + d]);
-                else cfma(t, u[3 * c + d], v[3 * s + d]);
-            }
-            w[3 * s + c] = ph * t;
+            for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    cpx<float> t = C(0.f, 0.f);
+#pragma unroll
+                    for (int d = 0; d < 3; ++d) {
+                        if (dag) cfma_cj(t, u[3 * d + c], v[3 * sp + d]);
+                        else cfma(t, u[3 * c + d], v[3 * sp + d]);
+                    }
+                    w[3 * sp + c] = ph * t;
+                }
         }
+        sink(b, w);
+    }
 }
 
 // ---------------------------------------------------------------------------
 // forward layer (also the input-gradient layer with adjoint weights)
+// Tile of PTC_LTILE = 64 sites (192 GEMM columns); thread t transports site
+// t % 64 for the channel group t / 64, so each (site, path) link is rebuilt by
+// at most two threads.  Warp w owns columns [48 w, 48 w + 48): 4 m-tiles x 6
+// n-tiles of m16n8 accumulators.
 // ---------------------------------------------------------------------------
 constexpr int LDW = 36;   // padded row length in 32-bit words (72 bf16)
 
@@ -119,9 +135,11 @@ __global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const u
                                                              const uint4* __restrict__ wemb, long ntiles) {
     extern __shared__ __align__(16) uint32_t sm[];
     uint32_t* Wsm = sm;                                // 9 x 64 rows x LDW words
-    uint32_t* Vsm = Wsm + 9 * 64 * LDW;                // 96 columns x LDW words
-    uint32_t* Osm = Vsm + PTC_N * LDW;                 // 32 sites x 8 ch x 12 complex (bf16 pairs)
+    uint32_t* Vsm = Wsm + 9 * 64 * LDW;                // 192 columns x LDW words
+    uint32_t* Osm = Vsm;                               // output staging reuses the V tile:
+                                                       // 64 sites x 8 ch x 12 complex (bf16 pairs)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
+    constexpr int CPG = (CIN + 1) / 2;                 // channels per transport group
 
     // weights: 9 x 64 x 64 bf16 = 9*64 rows of 8 uint4
     for (int e = tid; e < 9 * 64 * 8; e += PTC_BS) {
@@ -130,32 +148,30 @@ __global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const u
         uint32_t* d = Wsm + row * LDW + 4 * q;
         d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
     }
-    // zero the V tile once (rows of absent input channels stay zero)
-    for (int e = tid; e < PTC_N * LDW; e += PTC_BS) Vsm[e] = 0u;
     __syncthreads();
 
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long x0 = tile * PTC_TILE;
-        float acc[4][3][4];
+        const long x0 = tile * PTC_LTILE;
+        // rows of absent input channels must read as zero (the tile also served as
+        // output staging for the previous tile)
+        if (CIN < 8) {
+            for (int e = tid; e < PTC_LN * LDW; e += PTC_BS) Vsm[e] = 0u;
+            __syncthreads();
+        }
+        float acc[4][6][4];
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-            for (int b = 0; b < 3; ++b)
+            for (int b = 0; b < 6; ++b)
 #pragma unroll
                 for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
 
+        const int j = tid % PTC_LTILE, grp = tid / PTC_LTILE;
+        const long x = x0 + j;
+        const int b0 = grp * CPG, nb = min(CPG, CIN - b0);
 #pragma unroll 1
         for (int p = 0; p < 9; ++p) {
-            // transport: items (site j, channel b)
-            for (int it = tid; it < PTC_TILE * CIN; it += PTC_BS) {
-                const int j = it % PTC_TILE, b = it / PTC_TILE;
-                const long x = x0 + j;
-                cpx<float> w[12];
-                if (x < g.V) transported(g, in, b, x, p, w);
-                else {
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) w[q] = C(0.f, 0.f);
-                }
+            auto sink = [&](int b, const cpx<float> (&w)[12]) {
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
                     uint32_t* col = Vsm + (3 * j + c) * LDW;
@@ -164,6 +180,16 @@ __global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const u
                         col[2 * b + h] = pack2(w[3 * (2 * h) + c].re, w[3 * (2 * h + 1) + c].re);
                         col[16 + 2 * b + h] = pack2(w[3 * (2 * h) + c].im, w[3 * (2 * h + 1) + c].im);
                     }
+                }
+            };
+            if (nb > 0) {
+                if (x < g.V) {
+                    transport_channels<CPG>(g, in, x, p, b0, nb, sink);
+                } else {
+                    cpx<float> z[12];
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) z[q] = C(0.f, 0.f);
+                    for (int k = 0; k < nb; ++k) sink(b0 + k, z);
                 }
             }
             __syncthreads();
@@ -180,11 +206,11 @@ __global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const u
                     a[mt][3] = r0[8 * LDW + 4];
                 }
 #pragma unroll
-                for (int nt = 0; nt < 3; ++nt) {
-                    const uint32_t* c0 = Vsm + (24 * warp + 8 * nt + gq) * LDW + 8 * kk + tq;
-                    const uint32_t b0 = c0[0], b1 = c0[4];
+                for (int nt = 0; nt < 6; ++nt) {
+                    const uint32_t* c0 = Vsm + (48 * warp + 8 * nt + gq) * LDW + 8 * kk + tq;
+                    const uint32_t b0v = c0[0], b1v = c0[4];
 #pragma unroll
-                    for (int mt = 0; mt < 4; ++mt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0, b1);
+                    for (int mt = 0; mt < 4; ++mt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0v, b1v);
                 }
             }
             __syncthreads();
@@ -193,21 +219,21 @@ __global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const u
 #pragma unroll
         for (int mt = 0; mt < 2; ++mt)
 #pragma unroll
-            for (int nt = 0; nt < 3; ++nt)
+            for (int nt = 0; nt < 6; ++nt)
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int m = 16 * mt + gq + 8 * (r >> 1);      // < 32: (a, s)
-                    const int n = 24 * warp + 8 * nt + 2 * tq + (r & 1);
-                    const int a = m >> 2, s = m & 3, j = n / 3, c = n % 3;
-                    Osm[(j * 8 + a) * 12 + 3 * s + c] = pack2(acc[mt][nt][r], acc[mt + 2][nt][r]);
+                    const int n = 48 * warp + 8 * nt + 2 * tq + (r & 1);
+                    const int a = m >> 2, sp = m & 3, jj = n / 3, c = n % 3;
+                    Osm[(jj * 8 + a) * 12 + 3 * sp + c] = pack2(acc[mt][nt][r], acc[mt + 2][nt][r]);
                 }
         __syncthreads();
-        for (int it = tid; it < PTC_TILE * COUT * 3; it += PTC_BS) {
-            const int j = it % PTC_TILE, rest = it / PTC_TILE, q = rest % 3, a = rest / 3;
-            const long x = x0 + j;
-            if (x < g.V) {
-                const uint32_t* o = Osm + (j * 8 + a) * 12 + 4 * q;
-                out[((long)a * 3 + q) * g.V + x] = make_uint4(o[0], o[1], o[2], o[3]);
+        for (int it = tid; it < PTC_LTILE * COUT * 3; it += PTC_BS) {
+            const int jj = it % PTC_LTILE, rest = it / PTC_LTILE, q = rest % 3, a = rest / 3;
+            const long xx = x0 + jj;
+            if (xx < g.V) {
+                const uint32_t* o = Osm + (jj * 8 + a) * 12 + 4 * q;
+                out[((long)a * 3 + q) * g.V + xx] = make_uint4(o[0], o[1], o[2], o[3]);
             }
         }
         __syncthreads();
@@ -242,22 +268,30 @@ __global__ void __launch_bounds__(PTC_BS) ptc_wgrad_kernel(PtcGeom g, const uint
     const long t0 = chunk * per, t1 = min(ntiles, t0 + per);
     for (long tile = t0; tile < t1; ++tile) {
         const long x0 = tile * PTC_TILE;
-        for (int it = tid; it < PTC_TILE * CIN; it += PTC_BS) {
-            const int j = it % PTC_TILE, b = it / PTC_TILE;
+        {
+            constexpr int CPG = (CIN + 3) / 4;   // channels per transport group (4 groups of 32 sites)
+            const int j = tid % PTC_TILE, grp = tid / PTC_TILE;
             const long x = x0 + j;
-            cpx<float> w[12];
-            if (x < g.V) transported(g, in, b, x, p, w);
-            else {
+            const int b0 = grp * CPG, nb = min(CPG, CIN - b0);
+            auto sink = [&](int b, const cpx<float> (&w)[12]) {
 #pragma unroll
-                for (int q = 0; q < 12; ++q) w[q] = C(0.f, 0.f);
-            }
+                for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
-            for (int s = 0; s < 4; ++s)
+                    for (int c = 0; c < 3; ++c) {
+                        VT16[(4 * b + sp) * 2 * LDG + 3 * j + c] = fb(w[3 * sp + c].re);
+                        VT16[(32 + 4 * b + sp) * 2 * LDG + 3 * j + c] = fb(w[3 * sp + c].im);
+                    }
+            };
+            if (nb > 0) {
+                if (x < g.V) {
+                    transport_channels<CPG>(g, in, x, p, b0, nb, sink);
+                } else {
+                    cpx<float> z[12];
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    VT16[(4 * b + s) * 2 * LDG + 3 * j + c] = fb(w[3 * s + c].re);
-                    VT16[(32 + 4 * b + s) * 2 * LDG + 3 * j + c] = fb(w[3 * s + c].im);
+                    for (int q = 0; q < 12; ++q) z[q] = C(0.f, 0.f);
+                    for (int k = 0; k < nb; ++k) sink(b0 + k, z);
                 }
+            }
         }
         for (int it = tid; it < PTC_TILE * COUT; it += PTC_BS) {
             const int j = it % PTC_TILE, a = it / PTC_TILE;
@@ -505,7 +539,7 @@ __global__ void ptc_gauss_odd(float4* e, long vh, unsigned long long seed, unsig
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static size_t layer_smem() { return (size_t)(9 * 64 * LDW + PTC_N * LDW + PTC_TILE * 8 * 12) * 4; }
+static size_t layer_smem() { return (size_t)(9 * 64 * LDW + PTC_LN * LDW) * 4; }
 
 template <int CIN, int COUT>
 static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const void* w, int nsm, cudaStream_t st) {
@@ -516,7 +550,7 @@ static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const vo
         if (e != cudaSuccess) return e;
         cfg = true;
     }
-    const long ntiles = (g.V + PTC_TILE - 1) / PTC_TILE;
+    const long ntiles = (g.V + PTC_LTILE - 1) / PTC_LTILE;
     const long grid = std::min<long>(ntiles, 2L * nsm);
     ptc_layer_kernel<CIN, COUT><<<(unsigned)grid, PTC_BS, layer_smem(), st>>>(
         g, reinterpret_cast<const uint4*>(in), reinterpret_cast<uint4*>(out), reinterpret_cast<const uint4*>(w),

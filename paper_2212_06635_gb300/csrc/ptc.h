@@ -5,7 +5,9 @@
 
 namespace tmk {
 
-constexpr int PTC_TILE = 32;               // sites per tile
+constexpr int PTC_TILE = 32;               // sites per tile of the weight-gradient kernel
+constexpr int PTC_LTILE = 64;              // sites per tile of the layer kernel
+constexpr int PTC_LN = 3 * PTC_LTILE;      // layer GEMM columns per tile (site, colour)
 constexpr int PTC_BS = 128;                // threads per block (4 warps)
 constexpr int PTC_N = 3 * PTC_TILE;        // GEMM columns per tile (site, colour)
 constexpr int PTC_MAXC = 8;                // channels per layer
