@@ -55,6 +55,25 @@ def mhat_bytes_per_site(prec):
     return k1, k2
 
 
+def max_over_ranks(seconds_or_ms, device=None):
+    """Largest value over the ranks of the default process group (identity when
+    no group is initialised).  device: where the reduction tensor lives (a CUDA
+    device for NCCL, None = CPU for gloo)."""
+    import torch
+    import torch.distributed as tdist
+    if not (tdist.is_available() and tdist.is_initialized()):
+        return float(seconds_or_ms)
+    t = torch.tensor([float(seconds_or_ms)], dtype=torch.float64, device=device)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_gbs(world, step_bytes, steps, seconds):
+    """Whole-job GB/s: every rank runs its own replica (weak scaling); the job
+    processed world * steps steps in the slowest rank's time."""
+    return world * step_bytes * steps / seconds / 1e9
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -234,12 +253,8 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
         barrier()
         clocks = clk.stop()
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            ms = float(t.item())
-        value = world * step_bytes * args.steps / (ms * 1e-3) / 1e9
+        ms = max_over_ranks(e0.elapsed_time(e1), dev if dist else None)
+        value = aggregate_gbs(world, step_bytes, args.steps, ms * 1e-3)
 
         # ---- dominant kernel against the roofline ------------------------------
         t1, t2 = tm.tm_kernel_times(ctx, tm.TM_QHAT_PLUS, prec, fin, reps=50)
@@ -267,12 +282,8 @@ def run_ours(args, rank, world, local_rank):
             tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, prec, fout, fin)
             tm.tm_field_export(ctx, prec, 1, hout, fout)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([e2e_s], device=dev)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = world * step_bytes * args.steps / e2e_s / 1e9
+        e2e_s = max_over_ranks(time.perf_counter() - t0, dev if dist else None)
+        e2e = aggregate_gbs(world, step_bytes, args.steps, e2e_s)
 
         # ---- seconds to true rel res 1e-10: chosen form vs FP64 CG ----------------
         tts = {}
