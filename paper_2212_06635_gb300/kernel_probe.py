@@ -22,6 +22,38 @@ PRECS = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
 
 
+def ptc_probe(dims, reps):
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    u = F.gauge_field(dims, 1001)
+    b = F.odd_spinor(dims, 2001)
+    ctx = tm.tm_create(dims, 0)
+    net = tm.tm_ptc_create([1, 8, 8, 8, 1])
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, 0.14, 1.69, mu=0.0015)
+        tm.tm_ptc_init(net, 0.5, 0.02, 1)
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        f = torch.empty(tm.tm_field_bytes(ctx, tm.TM_F32, 1), dtype=torch.uint8, device="cuda")
+        o = torch.empty_like(f)
+        tm.tm_field_import(ctx, tm.TM_F32, 1, f, bd)
+        tm.tm_ptc_apply(net, ctx, o, f)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            tm.tm_ptc_apply(net, ctx, o, f)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(reps, 1)
+        print(f"dims {dims} PTC 1-8-8-8-1 forward: {ms:.3f} ms per application")
+    finally:
+        tm.tm_ptc_destroy(net)
+        tm.tm_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
@@ -30,11 +62,16 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--variant", default="direct", choices=["direct", "staged", "auto"],
                     help="stencil kernel variant of both passes (auto = tm_autotune)")
+    ap.add_argument("--ptc", action="store_true",
+                    help="instead: apply a 1-8-8-8-1 PTC network (1 + reps) times; each application "
+                         "launches its 4 layer kernels in order")
     a = ap.parse_args()
     import torch
     from paper_2212_06635_gb300 import tm
     from synth import fields as F
     dims = tuple(a.dims)
+    if a.ptc:
+        return ptc_probe(dims, a.reps)
     prec = PRECS[a.prec]
     nf = 2 if a.heavy else 1
     u = F.gauge_field(dims, 1001)
