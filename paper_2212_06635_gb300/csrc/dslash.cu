@@ -47,12 +47,14 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
     for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true>(acc[f], psi + 12 * f, u, ph_b);
 }
 
-// Resident blocks the compiler must fit per SM.  The light 16-bit odd pass fits
-// in 96 registers without spilling, which raises occupancy from 4 to 5 blocks of
-// 128 threads; every other pass spills at that bound and keeps the default.
+// Resident blocks the compiler must fit per SM.  Both light 16-bit passes fit in
+// 96 registers (spilling at most 16 B; the even pass streams its inverse blocks
+// two rows at a time for this), which raises occupancy from 4 to 5 blocks of
+// 128 threads.  FP32, FP64 and heavy passes spill heavily at such bounds and keep
+// the default.
 template <int P, int NF, int KIND>
 constexpr int dslash_min_blocks() {
-    return ((P == PF16 || P == PB16) && NF == 1 && KIND == K2_OE_LOCAL) ? 5 : 1;
+    return ((P == PF16 || P == PB16) && NF == 1) ? 5 : 1;
 }
 
 template <int P, int NF, int KIND, int NP, int BS>
@@ -89,11 +91,26 @@ __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash
                 for (int cb = 0; cb < 2; ++cb) {
                     cpx<R> v[6], w[6];
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) v[j] = acc[0][2 * cb + j / 3][j % 3];
-                    R m[72];
-                    load_reals<P, 72>(pr.clov, pr.g.vh, i, 72 * cb, m);
-                    if (pr.sign > 0) full6_mv<R, false>(w, m, v);
-                    else full6_mv<R, true>(w, m, v);
+                    for (int j = 0; j < 6; ++j) {
+                        v[j] = acc[0][2 * cb + j / 3][j % 3];
+                        w[j] = C((R)0, (R)0);
+                    }
+                    // stream the block two rows (24 reals) at a time to bound registers
+#pragma unroll
+                    for (int rr = 0; rr < 3; ++rr) {
+                        R m[24];
+                        load_reals<P, 24>(pr.clov, pr.g.vh, i, 72 * cb + 24 * rr, m);
+#pragma unroll
+                        for (int r2 = 0; r2 < 2; ++r2) {
+                            const int r = 2 * rr + r2;
+#pragma unroll
+                            for (int j = 0; j < 6; ++j) {
+                                const cpx<R> e = C(m[2 * (6 * r2 + j)], m[2 * (6 * r2 + j) + 1]);
+                                if (pr.sign > 0) cfma(w[r], e, v[j]);       // B v
+                                else cfma_cj(w[j], e, v[r]);                // B^dagger v
+                            }
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
                 }
@@ -143,14 +160,11 @@ __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash
                         w[j] = w[j] - k2 * acc[f][2 * cb + j / 3][j % 3];
                     }
                     herm6_mv_acc<R>(w, m + 36 * cb, v);
+                    const R rh = (R)pr.rho;   // W_hat = Q_hat + i rho (eq:hWpm), added after g5
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) out[12 * f + 6 * cb + j] = (cb == 0) ? w[j] : -w[j];
+                    for (int j = 0; j < 6; ++j)
+                        out[12 * f + 6 * cb + j] = ((cb == 0) ? w[j] : -w[j]) + rh * mul_i(v[j]);
                 }
-            }
-            if (pr.rho != 0.0) {   // W_hat = Q_hat + i rho (eq:hWpm)
-                const R rh = (R)pr.rho;
-#pragma unroll
-                for (int q = 0; q < NF * 12; ++q) out[q] = out[q] + rh * mul_i(psi[q]);
             }
             if (pr.partial != nullptr) {
                 R s = (R)0;

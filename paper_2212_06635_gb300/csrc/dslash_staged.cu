@@ -304,14 +304,11 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
                         w[j] = w[j] - k2 * acc[f][2 * cb + j / 3][j % 3];
                     }
                     herm6_mv_acc<R>(w, m + 36 * cb, v);
+                    const R rh = (R)pr.rho;   // W_hat = Q_hat + i rho (eq:hWpm), added after g5
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) out[12 * f + 6 * cb + j] = (cb == 0) ? w[j] : -w[j];
+                    for (int j = 0; j < 6; ++j)
+                        out[12 * f + 6 * cb + j] = ((cb == 0) ? w[j] : -w[j]) + rh * mul_i(v[j]);
                 }
-            }
-            if (pr.rho != 0.0) {   // W_hat = Q_hat + i rho (eq:hWpm)
-                const R rh = (R)pr.rho;
-#pragma unroll
-                for (int q = 0; q < NC; ++q) out[q] = out[q] + rh * mul_i(psi[q]);
             }
             if (pr.partial != nullptr) {
                 R s = (R)0;
