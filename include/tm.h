@@ -226,6 +226,11 @@ tm_status tm_ptc_init(tm_ptc* net, double scale, double noise, unsigned long lon
 tm_status tm_ptc_get_weights(const tm_ptc* net, double* weights);
 /* out = N(in): native FP32 light odd fields of ctx's lattice (device), stream-ordered. */
 tm_status tm_ptc_apply(tm_ptc* net, tm_ctx* ctx, void* out, const void* in, void* stream);
+/* Wait for the network's work queued on stream and report a layer kernel whose
+ * bounded wait on the tensor cores ran out (TM_ERR_TIMEOUT; its output is then
+ * incomplete).  tm_ptc_grad, tm_ptc_train and tm_solve_fcg check the same flag
+ * before they return. */
+tm_status tm_ptc_sync(tm_ptc* net, void* stream);
 /* Loss L = ||N(r) - e||^2 / ||e||^2 of one pair (canonical FP64 r, e; host or
  * device) and its Wirtinger gradient dL/dconj(W) (host, canonical weight layout). */
 tm_status tm_ptc_grad(tm_ptc* net, tm_ctx* ctx, const double* r, const double* e, double* loss,

@@ -1411,6 +1411,7 @@ struct tm_ptc {
     void* r32 = nullptr;       // training residual  (FP32 native odd)
     void* tmp32[2] = {};
     int nsm = 0;
+    int* derr = nullptr;       // set by a layer kernel whose tensor-core wait ran out of its bound
 };
 
 static size_t ptc_nw(const tm_ptc* n, int l) { return (size_t)9 * n->ch[l + 1] * n->ch[l] * 16; }
@@ -1455,6 +1456,8 @@ extern "C" tm_status tm_ptc_create(tm_ptc** out, int nlayers, const int* channel
     CK(cudaMalloc(&n->wpart, sizeof(float) * 9 * 4096 * n->nchunk));
     CK(cudaMalloc(&n->dscal, sizeof(double) * 8));
     CK(cudaMallocHost(&n->hscal, sizeof(double) * 8));
+    CK(cudaMalloc(&n->derr, sizeof(int)));
+    CK(cudaMemset(n->derr, 0, sizeof(int)));
     CKS(ptc_embed_all(n, nullptr));
     CK(cudaDeviceSynchronize());
     *out = n;
@@ -1482,6 +1485,7 @@ extern "C" tm_status tm_ptc_destroy(tm_ptc* n) {
     cudaFree(n->wpart);
     cudaFree(n->dscal);
     cudaFreeHost(n->hscal);
+    cudaFree(n->derr);
     delete n;
     return TM_OK;
 }
@@ -1596,7 +1600,7 @@ static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaS
     const PtcGeom g = ptc_geom(c);
     CK(launch_ptc_embed_odd(P32, r, n->act[0], g, st));
     for (int l = 0; l < n->L; ++l)
-        CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, st));
+        CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, n->derr, st));
     if (z) CK(launch_ptc_extract_odd(P32, n->act[n->L], z, g, st));
     return TM_OK;
 }
@@ -1609,7 +1613,8 @@ static tm_status ptc_backward(tm_ptc* n, tm_ctx* c, const void* e, float scale, 
     for (int l = n->L - 1; l >= 0; --l) {
         CK(launch_ptc_wgrad(n->ch[l], n->ch[l + 1], g, n->act[l], n->del[cur], n->wpart, n->nchunk, n->G[l], scale, st));
         if (l > 0) {
-            CK(launch_ptc_layer(n->ch[l + 1], n->ch[l], g, n->del[cur], n->del[1 - cur], n->wa[l], n->nsm, st));
+            CK(launch_ptc_layer(n->ch[l + 1], n->ch[l], g, n->del[cur], n->del[1 - cur], n->wa[l], n->nsm, n->derr,
+                                st));
             cur = 1 - cur;
         }
     }
@@ -1621,6 +1626,24 @@ static tm_status ptc_prepare(tm_ptc* n, tm_ctx* c, cudaStream_t st) {
     CKS(ensure_prec(c, PF16, st));
     CKS(ensure_prec(c, P32, st));
     return ptc_buffers(n, c);
+}
+
+// after a synchronisation: report (and clear) a layer wait that ran out of its bound
+static tm_status ptc_check_flag(tm_ptc* n) {
+    int h = 0;
+    CK(cudaMemcpy(&h, n->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (h != 0) {
+        CK(cudaMemset(n->derr, 0, sizeof(int)));
+        return fail(TM_ERR_TIMEOUT, "PTC layer: a wait on the tensor cores ran out of its bound");
+    }
+    return TM_OK;
+}
+
+extern "C" tm_status tm_ptc_sync(tm_ptc* n, void* stream) {
+    if (!n) return fail(TM_ERR_ARG, "tm_ptc_sync: null argument");
+    CK(cudaSetDevice(n->device));
+    CK(cudaStreamSynchronize(S(stream)));
+    return ptc_check_flag(n);
 }
 
 extern "C" tm_status tm_ptc_apply(tm_ptc* n, tm_ctx* c, void* out, const void* in, void* stream) {
@@ -1650,6 +1673,7 @@ extern "C" tm_status tm_ptc_grad(tm_ptc* n, tm_ctx* c, const double* r, const do
     CKS(ptc_backward(n, c, n->e32, 1.0f, st));
     CK(cudaMemcpyAsync(n->hscal, n->dscal, sizeof(double) * 2, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
+    CKS(ptc_check_flag(n));
     *loss = n->hscal[1] / n->hscal[0];
     size_t off = 0;
     for (int l = 0; l < n->L; ++l) {
@@ -1707,6 +1731,7 @@ extern "C" tm_status tm_ptc_train(tm_ptc* n, tm_ctx** cs, int nctx, tm_op op, in
     CK(cudaMemcpyAsync(h.data(), dloss, sizeof(double) * 2 * npairs, cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     cudaFree(dloss);
+    CKS(ptc_check_flag(n));
     if (losses)
         for (int k = 0; k < npairs; ++k) losses[k] = h[2 * k + 1] / h[2 * k];
     return status;
@@ -1875,6 +1900,7 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     CKS(stage_out(c, 1, x, WS_STAGE_X, x64, st));
     CK(cudaStreamSynchronize(st));
     info->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    CKS(ptc_check_flag(n));
     if (status != TM_OK) return fail(status, "tm_solve_fcg: %s", status == TM_ERR_BREAKDOWN ? "breakdown" : "not converged");
     return TM_OK;
 }

@@ -12,8 +12,10 @@
 //   rows (re/im, a<8, s<4), K = (re/im, b<8, t<4), columns (site, colour),
 //   A_p = [[Re W, -Im W], [Im W, Re W]] (BF16), V_p = T_p in (BF16), FP32 accumulate.
 // The transport (gather of neighbour activations, SU(3) multiply) fills V_p in
-// shared memory and mma.sync m16n8k16 (BF16 in, FP32 accumulate) does the mixing.
-// Channel counts below 8 are zero-padded in A_p.  Activations are BF16, layout
+// shared memory; the mixing runs on the tcgen05 tensor cores with the
+// accumulators in tensor memory (ptc_layer_tc).  The weight gradient uses
+// mma.sync m16n8k16 (BF16 in, FP32 accumulate) with channel counts below 8
+// zero-padded.  Activations are BF16, layout
 // [channel][3 x 16-B vectors of 4 complex (spin, colour)][V] in lexicographic site
 // order.  The input gradient of a layer is the same layer run with the adjoint
 // weights W'_p = (W_{rev p})^H (T_p^dag = T_{rev p}); the weight gradient is the
@@ -121,122 +123,281 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 }
 
 // ---------------------------------------------------------------------------
-// forward layer (also the input-gradient layer with adjoint weights)
-// Tile of PTC_LTILE = 64 sites (192 GEMM columns); thread t transports site
-// t % 64 for the channel group t / 64, so each (site, path) link is rebuilt by
-// at most two threads.  Warp w owns columns [48 w, 48 w + 48): 4 m-tiles x 6
-// n-tiles of m16n8 accumulators.
+// forward layer (also the input-gradient layer with adjoint weights) on the
+// fifth-generation tensor cores.  Per tile of TC_M = 128 sites and per path p,
+// colour c:  D_c[site][n] += A_{p,c}[site][k] * B_p[n][k]  (kind::f16, BF16 in,
+// FP32 accumulate in tensor memory), M = 128 sites, N = 8 COUT (re/im, spin,
+// output channel), K = 8 CIN (re/im, spin, input channel).  A is the transported
+// input written to shared memory by all threads; B (the embedded weights of all
+// 9 paths) stays resident in shared memory; one thread issues the MMAs, which run
+// asynchronously while the threads transport the next path into the other of
+// two stage buffers.  The accumulators of a tile (3 N columns) live in TMEM and
+// are read back with tcgen05.ld: TMEM lane = site, so each thread of the
+// epilogue owns one site and writes its output vectors directly.
+//
+// Shared-memory operand images are the canonical K-major layout without
+// swizzle: core matrices of 8 rows x 16 bytes (8 BF16 along K) stored as 128
+// contiguous bytes; core matrices adjacent along K are LBO = 128 bytes apart,
+// 8-row groups along M/N are SBO = 128 * KCH bytes apart (KCH 16-byte K chunks,
+// one per input channel: its 4 spins as (re, im) pairs).
 // ---------------------------------------------------------------------------
-constexpr int LDW = 36;   // padded row length in 32-bit words (72 bf16)
+constexpr int TC_M = 128;                  // sites per tile = MMA M = TMEM lanes
+constexpr int TC_BS = 512;                 // threads per block: 4 site groups of 128
+constexpr int TC_STAGES = 2;               // transport stage buffers
+constexpr long long TC_WAIT_NS = 1000000000LL;   // bound on every mbarrier wait (1 s)
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(PTC_BS, 2) ptc_layer_kernel(PtcGeom g, const uint4* __restrict__ in,
-                                                             uint4* __restrict__ out,
-                                                             const uint4* __restrict__ wemb, long ntiles) {
-    extern __shared__ __align__(16) uint32_t sm[];
-    uint32_t* Wsm = sm;                                // 9 x 64 rows x LDW words
-    uint32_t* Vsm = Wsm + 9 * 64 * LDW;                // 192 columns x LDW words
-    uint32_t* Osm = Vsm;                               // output staging reuses the V tile:
-                                                       // 64 sites x 8 ch x 12 complex (bf16 pairs)
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    constexpr int CPG = (CIN + 1) / 2;                 // channels per transport group
+struct TcShape {
+    static constexpr int KCH = CIN < 2 ? 2 : CIN;            // K = 8 KCH >= 16 (one MMA K step)
+    static constexpr int NN = 8 * COUT < 16 ? 16 : 8 * COUT; // N per colour (multiple of 16 for M = 128)
+    static constexpr int NPS = CIN >= 4 ? 1 : 4 / CIN;       // paths per stage (small CIN: one path per group)
+    static constexpr int GPP = 4 / NPS;                      // site groups per path
+    static constexpr int CPG = CIN / GPP;                    // input channels per thread
+    static constexpr int NSTG = (9 + NPS - 1) / NPS;         // stages per tile
+    static constexpr int A_COL = TC_M * 16 * KCH;            // bytes of one (path, colour) A image
+    static constexpr int A_STAGE = NPS * 3 * A_COL;
+    static constexpr int W_PATH = NN * 16 * KCH;             // bytes of one path's B image
+    static constexpr int W_ALL = 9 * W_PATH;
+    static constexpr int TMEM_COLS = 3 * NN <= 32 ? 32 : (3 * NN <= 64 ? 64 : (3 * NN <= 128 ? 128 : 256));
+    static constexpr int SMEM = W_ALL + TC_STAGES * A_STAGE + 64;   // + mbarriers, TMEM address, abort flag
+    // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
+    // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) |
+                                      ((uint32_t)(TC_M >> 4) << 24);
+};
 
-    // weights: 9 x 64 x 64 bf16 = 9*64 rows of 8 uint4
-    for (int e = tid; e < 9 * 64 * 8; e += PTC_BS) {
-        const uint4 v = __ldg(wemb + e);
-        const int row = e >> 3, q = e & 7;
-        uint32_t* d = Wsm + row * LDW + 4 * q;
-        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, LBO, SBO (>> 4), version 1 at bit 46, no swizzle
+__device__ __forceinline__ uint64_t smem_desc(uint32_t start, uint32_t lbo, uint32_t sbo) {
+    return (uint64_t)((start & 0x3FFFFu) >> 4) | ((uint64_t)((lbo & 0x3FFFFu) >> 4) << 16) |
+           ((uint64_t)((sbo & 0x3FFFFu) >> 4) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ long long global_ns() {
+    long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// wait for the completion of the phase with this parity; false after TC_WAIT_NS
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+    if (mbar_test(b, parity)) return true;
+    const long long t0 = global_ns();
+    while (!mbar_test(b, parity))
+        if (global_ns() - t0 > TC_WAIT_NS) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tc_mma(uint32_t dtmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+// arrive once on the mbarrier when every MMA this thread issued so far has completed
+__device__ __forceinline__ void tc_commit(uint64_t* b) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(b))
+                 : "memory");
+}
+
+// 8 consecutive FP32 columns of this warp's 32 TMEM lanes (lane = thread)
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr)
+                 : "memory");
+}
+
+// completes the loads above; the registers are tied in so no use moves ahead of it
+__device__ __forceinline__ void tmem_wait_ld(uint32_t (&a)[8], uint32_t (&b)[8], uint32_t (&c)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7]),
+                   "+r"(b[0]), "+r"(b[1]), "+r"(b[2]), "+r"(b[3]), "+r"(b[4]), "+r"(b[5]), "+r"(b[6]), "+r"(b[7]),
+                   "+r"(c[0]), "+r"(c[1]), "+r"(c[2]), "+r"(c[3]), "+r"(c[4]), "+r"(c[5]), "+r"(c[6]), "+r"(c[7])
+                 :
+                 : "memory");
+}
+
+__device__ __forceinline__ uint32_t pack_f32bits(uint32_t re, uint32_t im) {
+    return pack2(__uint_as_float(re), __uint_as_float(im));
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4* __restrict__ in,
+                                                        uint4* __restrict__ out, const uint4* __restrict__ wimg,
+                                                        long ntiles, int* err) {
+    using S = TcShape<CIN, COUT>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* Wsm = smem;                                   // 9 paths of B images
+    uint8_t* Asm = smem + S::W_ALL;                        // TC_STAGES stage buffers of A images
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Asm + TC_STAGES * S::A_STAGE);   // [0, 1] stages, [2] drain
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // resident weights; the K padding chunk of one-channel inputs must read as zero
+    for (int e = tid; e < S::W_ALL / 16; e += TC_BS) reinterpret_cast<uint4*>(Wsm)[e] = __ldg(wimg + e);
+    if (CIN == 1) {
+        for (int e = tid; e < TC_STAGES * S::NPS * 3 * TC_M; e += TC_BS) {
+            const int r = e % TC_M, col = e / TC_M;   // (stage, path, colour) image, row r
+            *reinterpret_cast<uint4*>(Asm + (long)col * S::A_COL + (r >> 3) * (128 * S::KCH) + 128 + (r & 7) * 16) =
+                make_uint4(0u, 0u, 0u, 0u);
+        }
     }
+    if (tid == 0) {
+        for (int k = 0; k < 3; ++k) mbar_init(bar + k, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"((uint32_t)S::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
     __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+
+    const int r = tid % TC_M, grp = tid / TC_M;            // transport: site r of the tile, site group
+    const int pi = grp / S::GPP;                           // path slot of this group within a stage
+    const int b0 = (grp % S::GPP) * S::CPG;                // first input channel of this thread
+    const uint32_t a_base = smem_addr(Asm), w_base = smem_addr(Wsm);
+    constexpr uint32_t SBO_A = 128 * S::KCH, SBO_W = 128 * S::KCH;
+    uint32_t u = 0;                                        // stages issued by this block so far
+    bool ok = true;
+    // The abort flag is set only just before a barrier (a wait that ran out) and
+    // read only just after one, so every thread reads the same value.
+    bool stop = false;
 
     for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long x0 = tile * PTC_LTILE;
-        // rows of absent input channels must read as zero (the tile also served as
-        // output staging for the previous tile)
-        if (CIN < 8) {
-            for (int e = tid; e < PTC_LN * LDW; e += PTC_BS) Vsm[e] = 0u;
+        const long x = tile * TC_M + r;
+        for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
+            const int buf = u % TC_STAGES;
+            // the MMAs that last read this buffer must be done before it is rewritten
+            if (u >= TC_STAGES && !mbar_wait(bar + buf, ((u / TC_STAGES) - 1) & 1)) {
+                ok = false;
+                *abort_flag = 1;
+            }
             __syncthreads();
-        }
-        float acc[4][6][4];
+            stop = *abort_flag != 0;
+            if (stop) break;
+            const int p = stg * S::NPS + pi;
+            if (p < 9 && x < g.V) {
+                uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * SBO_A + (r & 7) * 16;
+                auto sink = [&](int b, const cpx<float> (&w)[12]) {
 #pragma unroll
-        for (int a = 0; a < 4; ++a)
-#pragma unroll
-            for (int b = 0; b < 6; ++b)
-#pragma unroll
-                for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
-
-        const int j = tid % PTC_LTILE, grp = tid / PTC_LTILE;
-        const long x = x0 + j;
-        const int b0 = grp * CPG, nb = min(CPG, CIN - b0);
+                    for (int c = 0; c < 3; ++c)
+                        *reinterpret_cast<uint4*>(img + c * S::A_COL + b * 128) =
+                            make_uint4(pack2(w[c].re, w[c].im), pack2(w[3 + c].re, w[3 + c].im),
+                                       pack2(w[6 + c].re, w[6 + c].im), pack2(w[9 + c].re, w[9 + c].im));
+                };
+                transport_channels<S::CPG>(g, in, x, p, b0, S::CPG, sink);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
 #pragma unroll 1
-        for (int p = 0; p < 9; ++p) {
-            auto sink = [&](int b, const cpx<float> (&w)[12]) {
+                for (int q = 0; q < S::NPS; ++q) {
+                    const int pp = stg * S::NPS + q;
+                    if (pp >= 9) break;
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    uint32_t* col = Vsm + (3 * j + c) * LDW;
+                    for (int c = 0; c < 3; ++c)
 #pragma unroll
-                    for (int h = 0; h < 2; ++h) {   // spins (2h, 2h+1)
-                        col[2 * b + h] = pack2(w[3 * (2 * h) + c].re, w[3 * (2 * h + 1) + c].re);
-                        col[16 + 2 * b + h] = pack2(w[3 * (2 * h) + c].im, w[3 * (2 * h + 1) + c].im);
+                        for (int kk = 0; kk < S::KCH / 2; ++kk) {
+                            const uint32_t as = a_base + buf * S::A_STAGE + (q * 3 + c) * S::A_COL + kk * 256;
+                            const uint32_t ws = w_base + pp * S::W_PATH + kk * 256;
+                            tc_mma(tmem + c * S::NN, smem_desc(as, 128, SBO_A), smem_desc(ws, 128, SBO_W), S::IDESC,
+                                   (pp > 0 || kk > 0) ? 1u : 0u);
+                        }
+                }
+                tc_commit(bar + buf);
+            }
+        }
+        if (stop) break;
+        // epilogue: all MMAs of the tile are behind the last commit
+        if (!mbar_wait(bar + (u - 1) % TC_STAGES, ((u - 1) / TC_STAGES) & 1)) {
+            ok = false;
+            *abort_flag = 1;
+        }
+        __syncthreads();
+        stop = *abort_flag != 0;
+        if (stop) break;
+        tc_fence_after();
+        __syncwarp();
+        {
+            const int quarter = warp & 3, wg = warp >> 2;
+            const long xo = tile * TC_M + 32 * quarter + lane;
+            constexpr int CPO = (COUT + 3) / 4;            // output channels per warp
+#pragma unroll
+            for (int k = 0; k < CPO; ++k) {
+                const int a = wg * CPO + k;
+                if (a < COUT) {                             // warp-uniform
+                    uint32_t v0[8], v1[8], v2[8];
+                    const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 8 * a;
+                    tmem_ld8(ta, v0);
+                    tmem_ld8(ta + S::NN, v1);
+                    tmem_ld8(ta + 2 * S::NN, v2);
+                    tmem_wait_ld(v0, v1, v2);
+                    if (xo < g.V) {
+                        // complex (s, c) at index 3 s + c; column 8 a + 2 s + ri of colour c
+                        uint32_t wv[12];
+#pragma unroll
+                        for (int s = 0; s < 4; ++s) {
+                            wv[3 * s + 0] = pack_f32bits(v0[2 * s], v0[2 * s + 1]);
+                            wv[3 * s + 1] = pack_f32bits(v1[2 * s], v1[2 * s + 1]);
+                            wv[3 * s + 2] = pack_f32bits(v2[2 * s], v2[2 * s + 1]);
+                        }
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            out[((long)a * 3 + q) * g.V + xo] =
+                                make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
                     }
                 }
-            };
-            if (nb > 0) {
-                if (x < g.V) {
-                    transport_channels<CPG>(g, in, x, p, b0, nb, sink);
-                } else {
-                    cpx<float> z[12];
-#pragma unroll
-                    for (int q = 0; q < 12; ++q) z[q] = C(0.f, 0.f);
-                    for (int k = 0; k < nb; ++k) sink(b0 + k, z);
-                }
-            }
-            __syncthreads();
-            const uint32_t* Wp = Wsm + p * 64 * LDW;
-#pragma unroll
-            for (int kk = 0; kk < 4; ++kk) {
-                uint32_t a[4][4];
-#pragma unroll
-                for (int mt = 0; mt < 4; ++mt) {
-                    const uint32_t* r0 = Wp + (16 * mt + gq) * LDW + 8 * kk + tq;
-                    a[mt][0] = r0[0];
-                    a[mt][1] = r0[8 * LDW];
-                    a[mt][2] = r0[4];
-                    a[mt][3] = r0[8 * LDW + 4];
-                }
-#pragma unroll
-                for (int nt = 0; nt < 6; ++nt) {
-                    const uint32_t* c0 = Vsm + (48 * warp + 8 * nt + gq) * LDW + 8 * kk + tq;
-                    const uint32_t b0v = c0[0], b1v = c0[4];
-#pragma unroll
-                    for (int mt = 0; mt < 4; ++mt) mma_bf16(acc[mt][nt], a[mt][0], a[mt][1], a[mt][2], a[mt][3], b0v, b1v);
-                }
-            }
-            __syncthreads();
-        }
-        // accumulators -> Osm as complex bf16 pairs [site][channel][s*3+c]
-#pragma unroll
-        for (int mt = 0; mt < 2; ++mt)
-#pragma unroll
-            for (int nt = 0; nt < 6; ++nt)
-#pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    const int m = 16 * mt + gq + 8 * (r >> 1);      // < 32: (a, s)
-                    const int n = 48 * warp + 8 * nt + 2 * tq + (r & 1);
-                    const int a = m >> 2, sp = m & 3, jj = n / 3, c = n % 3;
-                    Osm[(jj * 8 + a) * 12 + 3 * sp + c] = pack2(acc[mt][nt][r], acc[mt + 2][nt][r]);
-                }
-        __syncthreads();
-        for (int it = tid; it < PTC_LTILE * COUT * 3; it += PTC_BS) {
-            const int jj = it % PTC_LTILE, rest = it / PTC_LTILE, q = rest % 3, a = rest / 3;
-            const long xx = x0 + jj;
-            if (xx < g.V) {
-                const uint32_t* o = Osm + (jj * 8 + a) * 12 + 4 * q;
-                out[((long)a * 3 + q) * g.V + xx] = make_uint4(o[0], o[1], o[2], o[3]);
             }
         }
-        __syncthreads();
+        tc_fence_before();
+        __syncthreads();   // TMEM reads done before the next tile's first MMA overwrites D
+    }
+
+    // drain: every MMA issued by this block completes before TMEM is released
+    __syncthreads();
+    if (tid == 0) {
+        tc_commit(bar + 2);
+        if (!mbar_wait(bar + 2, 0)) ok = false;
+    }
+    if (!ok) atomicExch(err, 1);
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS)
+                     : "memory");
     }
 }
 
@@ -364,30 +525,41 @@ __global__ void ptc_wgrad_reduce(const float* __restrict__ partial, int nchunk, 
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int rev_path(int p) { return p == 0 ? 0 : (p <= 4 ? p + 4 : p - 4); }
 
-__global__ void ptc_embed_weights(const float2* __restrict__ W, int cin, int cout, uint16_t* fwd, uint16_t* adj) {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;   // over 9 x 64 x 64
-    if (e >= 9 * 64 * 64) return;
-    const int k = e & 63, m = (e >> 6) & 63, p = e >> 12;
-    const int rim = m >> 5, cim = k >> 5;
-    {   // forward: m = (ri, a, s), k = (ri', b, t)
-        const int a = (m & 31) >> 2, s = m & 3, b = (k & 31) >> 2, t = k & 3;
-        float v = 0.f;
-        if (a < cout && b < cin) {
-            const float2 w = W[(((p * cout + a) * cin + b) * 4 + s) * 4 + t];
-            v = (rim == cim) ? w.x : (rim == 0 ? -w.y : w.y);
+// B image of one layer for ptc_layer_tc, layer shape cin_l -> cout_l: per path p,
+// row n = 8 a + 2 s + ri (output channel a, spin s, re/im) and K index
+// k = 8 b + 2 t + ri' (input channel b, spin t, re/im), stored as
+// [p][n / 8][k / 8][n % 8][k % 8] BF16 with NN = max(16, 8 cout_l) rows and
+// 8 max(2, cin_l) K entries, zero beyond the layer's channels.  Real embedding of
+// the complex weight w: (re, re) -> Re w, (re, im) -> -Im w, (im, re) -> Im w,
+// (im, im) -> Re w.  The adjoint image (input gradient) is the layer cout -> cin
+// with W'_p[b][a][t][s] = conj(W_{rev p}[a][b][s][t]).
+__global__ void ptc_embed_weights(const float2* __restrict__ W, int cin, int cout, int adjoint, uint16_t* img) {
+    const int cin_l = adjoint ? cout : cin, cout_l = adjoint ? cin : cout;
+    const int kch = cin_l < 2 ? 2 : cin_l, nn = 8 * cout_l < 16 ? 16 : 8 * cout_l;
+    const int per_path = nn * 8 * kch;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= 9 * per_path) return;
+    const int p = e / per_path;
+    int rem = e - p * per_path;
+    const int kr = rem & 7; rem >>= 3;   // k % 8
+    const int nr = rem & 7; rem >>= 3;   // n % 8
+    const int kc = rem % kch;            // k / 8
+    const int ng = rem / kch;            // n / 8
+    const int n = 8 * ng + nr, k = 8 * kc + kr;
+    const int ao = n >> 3, so = (n >> 1) & 3, rim = n & 1;   // output channel, spin, re/im
+    const int bi = k >> 3, si = (k >> 1) & 3, cim = k & 1;   // input channel, spin, re/im
+    float v = 0.f;
+    if (ao < cout_l && bi < cin_l) {
+        float2 w;
+        if (!adjoint) {
+            w = W[(((p * cout + ao) * cin + bi) * 4 + so) * 4 + si];
+        } else {
+            const float2 w0 = W[(((rev_path(p) * cout + bi) * cin + ao) * 4 + si) * 4 + so];
+            w = make_float2(w0.x, -w0.y);
         }
-        fwd[e] = fb(v);
+        v = (rim == cim) ? w.x : (rim == 0 ? -w.y : w.y);
     }
-    {   // adjoint: W'_p[b][a][t][s] = conj(W_{rev p}[a][b][s][t]); m = (ri, b, t), k = (ri', a, s)
-        const int b = (m & 31) >> 2, t = m & 3, a = (k & 31) >> 2, s = k & 3;
-        float v = 0.f;
-        if (a < cout && b < cin) {
-            const float2 w0 = W[(((rev_path(p) * cout + a) * cin + b) * 4 + s) * 4 + t];
-            const float2 w = make_float2(w0.x, -w0.y);
-            v = (rim == cim) ? w.x : (rim == 0 ? -w.y : w.y);
-        }
-        adj[e] = fb(v);
-    }
+    img[e] = fb(v);
 }
 
 // Adam (Kingma & Ba) on re and im parts; grad is zeroed after the step
@@ -539,37 +711,40 @@ __global__ void ptc_gauss_odd(float4* e, long vh, unsigned long long seed, unsig
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static size_t layer_smem() { return (size_t)(9 * 64 * LDW + PTC_LN * LDW) * 4; }
-
 template <int CIN, int COUT>
-static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const void* w, int nsm, cudaStream_t st) {
-    static bool cfg = false;
-    if (!cfg) {
-        cudaError_t e = cudaFuncSetAttribute(ptc_layer_kernel<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)layer_smem());
+static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const void* w, int nsm, int* err,
+                           cudaStream_t st) {
+    using S = TcShape<CIN, COUT>;
+    static_assert(S::SMEM <= 227 * 1024, "layer shared memory");
+    static int cfg_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (cfg_dev != dev) {
+        e = cudaFuncSetAttribute(ptc_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
         if (e != cudaSuccess) return e;
-        cfg = true;
+        cfg_dev = dev;
     }
-    const long ntiles = (g.V + PTC_LTILE - 1) / PTC_LTILE;
-    const long grid = std::min<long>(ntiles, 2L * nsm);
-    ptc_layer_kernel<CIN, COUT><<<(unsigned)grid, PTC_BS, layer_smem(), st>>>(
+    const long ntiles = (g.V + TC_M - 1) / TC_M;
+    const long grid = std::min<long>(ntiles, nsm);
+    ptc_layer_tc<CIN, COUT><<<(unsigned)grid, TC_BS, S::SMEM, st>>>(
         g, reinterpret_cast<const uint4*>(in), reinterpret_cast<uint4*>(out), reinterpret_cast<const uint4*>(w),
-        ntiles);
+        ntiles, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* w, int nsm,
-                             cudaStream_t st) {
-    if (cin == 1 && cout == 8) return layer_t<1, 8>(g, in, out, w, nsm, st);
-    if (cin == 8 && cout == 8) return layer_t<8, 8>(g, in, out, w, nsm, st);
-    if (cin == 8 && cout == 1) return layer_t<8, 1>(g, in, out, w, nsm, st);
-    if (cin == 1 && cout == 1) return layer_t<1, 1>(g, in, out, w, nsm, st);
-    if (cin == 1 && cout == 2) return layer_t<1, 2>(g, in, out, w, nsm, st);
-    if (cin == 2 && cout == 2) return layer_t<2, 2>(g, in, out, w, nsm, st);
-    if (cin == 2 && cout == 1) return layer_t<2, 1>(g, in, out, w, nsm, st);
-    if (cin == 4 && cout == 4) return layer_t<4, 4>(g, in, out, w, nsm, st);
-    if (cin == 1 && cout == 4) return layer_t<1, 4>(g, in, out, w, nsm, st);
-    if (cin == 4 && cout == 1) return layer_t<4, 1>(g, in, out, w, nsm, st);
+                             int* err, cudaStream_t st) {
+    if (cin == 1 && cout == 8) return layer_t<1, 8>(g, in, out, w, nsm, err, st);
+    if (cin == 8 && cout == 8) return layer_t<8, 8>(g, in, out, w, nsm, err, st);
+    if (cin == 8 && cout == 1) return layer_t<8, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 1 && cout == 1) return layer_t<1, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 1 && cout == 2) return layer_t<1, 2>(g, in, out, w, nsm, err, st);
+    if (cin == 2 && cout == 2) return layer_t<2, 2>(g, in, out, w, nsm, err, st);
+    if (cin == 2 && cout == 1) return layer_t<2, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 4 && cout == 4) return layer_t<4, 4>(g, in, out, w, nsm, err, st);
+    if (cin == 1 && cout == 4) return layer_t<1, 4>(g, in, out, w, nsm, err, st);
+    if (cin == 4 && cout == 1) return layer_t<4, 1>(g, in, out, w, nsm, err, st);
     return cudaErrorInvalidValue;
 }
 
@@ -604,8 +779,10 @@ cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in
 }
 
 cudaError_t launch_ptc_embed_weights(const float2* W, int cin, int cout, void* fwd, void* adj, cudaStream_t st) {
-    ptc_embed_weights<<<9 * 64 * 64 / 256, 256, 0, st>>>(W, cin, cout, reinterpret_cast<uint16_t*>(fwd),
-                                                          reinterpret_cast<uint16_t*>(adj));
+    ptc_embed_weights<<<9 * 64 * 64 / 256, 256, 0, st>>>(W, cin, cout, 0, reinterpret_cast<uint16_t*>(fwd));
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ptc_embed_weights<<<9 * 64 * 64 / 256, 256, 0, st>>>(W, cin, cout, 1, reinterpret_cast<uint16_t*>(adj));
     return cudaGetLastError();
 }
 

@@ -6,8 +6,6 @@
 namespace tmk {
 
 constexpr int PTC_TILE = 32;               // sites per tile of the weight-gradient kernel
-constexpr int PTC_LTILE = 64;              // sites per tile of the layer kernel
-constexpr int PTC_LN = 3 * PTC_LTILE;      // layer GEMM columns per tile (site, colour)
 constexpr int PTC_BS = 128;                // threads per block (4 warps)
 constexpr int PTC_N = 3 * PTC_TILE;        // GEMM columns per tile (site, colour)
 constexpr int PTC_MAXC = 8;                // channels per layer
@@ -19,8 +17,10 @@ struct PtcGeom {
     const void* gauge[2];   // FP16 native links per parity
 };
 
+// one layer on the tensor cores; *err is set to 1 if a wait on the tensor cores ran
+// out of its bound (the layer's output is then incomplete)
 cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* wemb,
-                             int nsm, cudaStream_t st);
+                             int nsm, int* err, cudaStream_t st);
 cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
                              int nchunk, float2* grad, float scale, cudaStream_t st);
 cudaError_t launch_ptc_embed_weights(const float2* W, int cin, int cout, void* fwd, void* adj, cudaStream_t st);

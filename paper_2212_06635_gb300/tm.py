@@ -91,6 +91,7 @@ _sigs = {
     "tm_ptc_init": [_vp, ct.c_double, ct.c_double, ct.c_ulonglong],
     "tm_ptc_get_weights": [_vp, _vp],
     "tm_ptc_apply": [_vp, _vp, _vp, _vp, _vp],
+    "tm_ptc_sync": [_vp, _vp],
     "tm_ptc_grad": [_vp, _vp, _vp, _vp, ct.POINTER(ct.c_double), _vp, _vp],
     "tm_ptc_train": [_vp, ct.POINTER(_vp), ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_ulonglong,
                      _vp, _vp],
@@ -306,6 +307,10 @@ def tm_ptc_get_weights(net):
 
 def tm_ptc_apply(net, ctx, out, inp, stream=None):
     _check(lib.tm_ptc_apply(net, ctx, ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_ptc_sync(net, stream=None):
+    _check(lib.tm_ptc_sync(net, _stream(stream)))
 
 
 def tm_ptc_grad(net, ctx, r, e, stream=None):

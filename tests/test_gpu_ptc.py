@@ -41,13 +41,16 @@ def _apply(tm, lat, net, r):
     o = lat.native(tm.TM_F32, 1)
     tm.tm_field_import(lat.ctx, tm.TM_F32, 1, a, src)
     tm.tm_ptc_apply(net, lat.ctx, o, a)
+    tm.tm_ptc_sync(net)   # raises if a layer's bounded tensor-core wait ran out
     out = src.clone()
     tm.tm_field_export(lat.ctx, tm.TM_F32, 1, out, o)
     torch.cuda.synchronize()
     return from_dev(out, r.shape)
 
 
-@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8)])
+# 10x10x12x18: 21600 sites = 168 full tiles of 128 and a ragged tail of 96,
+# more tiles than SMs, so blocks loop over several tiles
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (10, 10, 12, 18)])
 def test_forward_matches_oracle(dims):
     u = F.gauge_field(dims, 21)
     lat = Lat(u, dims, KAPPA, CSW, mu=MU)
