@@ -127,13 +127,21 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 // fifth-generation tensor cores.  Per tile of TC_M = 128 sites and per path p,
 // colour c:  D_c[site][n] += A_{p,c}[site][k] * B_p[n][k]  (kind::f16, BF16 in,
 // FP32 accumulate in tensor memory), M = 128 sites, N = 8 COUT (re/im, spin,
-// output channel), K = 8 CIN (re/im, spin, input channel).  A is the transported
-// input written to shared memory by all threads; B (the embedded weights of all
-// 9 paths) stays resident in shared memory; one thread issues the MMAs, which run
-// asynchronously while the threads transport the next path into the other of
-// two stage buffers.  The accumulators of a tile (3 N columns) live in TMEM and
-// are read back with tcgen05.ld: TMEM lane = site, so each thread of the
-// epilogue owns one site and writes its output vectors directly.
+// output channel), K = 8 CIN (re/im, spin, input channel).
+//
+// Warp roles: 16 transport warps (4 threads per site) gather and transport the
+// input of one stage (one or more paths) into one of two stage buffers and
+// arrive on its "full" mbarrier.  Each thread's activation words for its next
+// stage are copied into a private shared-memory slot by cp.async (and its link
+// words into registers) while it transports the current stage; a channel's copy
+// is issued once the channel's current words have been consumed.  One MMA warp waits for
+// "full", issues the stage's MMAs from one thread and commits them to the
+// buffer's "empty" mbarrier, so transport and MMAs overlap.  After a tile's last
+// stage the MMA warp commits to "acc_full"; the transport warps read the
+// accumulators back with tcgen05.ld (TMEM lane = site, so each thread owns one
+// site and writes its output vectors directly) and arrive on "acc_empty" before
+// the next tile's first MMA overwrites them.  The 9 paths' embedded weights (B)
+// stay resident in shared memory.
 //
 // Shared-memory operand images are the canonical K-major layout without
 // swizzle: core matrices of 8 rows x 16 bytes (8 BF16 along K) stored as 128
@@ -142,7 +150,9 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 // one per input channel: its 4 spins as (re, im) pairs).
 // ---------------------------------------------------------------------------
 constexpr int TC_M = 128;                  // sites per tile = MMA M = TMEM lanes
-constexpr int TC_BS = 512;                 // threads per block: 4 site groups of 128
+constexpr int TC_G = 4;                    // site groups (transport threads per site)
+constexpr int TC_PT = TC_G * 128;          // transport threads
+constexpr int TC_BS = TC_PT + 32;          // + the MMA warp
 constexpr int TC_STAGES = 2;               // transport stage buffers
 constexpr long long TC_WAIT_NS = 1000000000LL;   // bound on every mbarrier wait (1 s)
 
@@ -150,8 +160,8 @@ template <int CIN, int COUT>
 struct TcShape {
     static constexpr int KCH = CIN < 2 ? 2 : CIN;            // K = 8 KCH >= 16 (one MMA K step)
     static constexpr int NN = 8 * COUT < 16 ? 16 : 8 * COUT; // N per colour (multiple of 16 for M = 128)
-    static constexpr int NPS = CIN >= 4 ? 1 : 4 / CIN;       // paths per stage (small CIN: one path per group)
-    static constexpr int GPP = 4 / NPS;                      // site groups per path
+    static constexpr int GPP = CIN < TC_G ? CIN : TC_G;      // site groups per path
+    static constexpr int NPS = TC_G / GPP;                   // paths per stage (small CIN: one path per group)
     static constexpr int CPG = CIN / GPP;                    // input channels per thread
     static constexpr int NSTG = (9 + NPS - 1) / NPS;         // stages per tile
     static constexpr int A_COL = TC_M * 16 * KCH;            // bytes of one (path, colour) A image
@@ -159,7 +169,8 @@ struct TcShape {
     static constexpr int W_PATH = NN * 16 * KCH;             // bytes of one path's B image
     static constexpr int W_ALL = 9 * W_PATH;
     static constexpr int TMEM_COLS = 3 * NN <= 32 ? 32 : (3 * NN <= 64 ? 64 : (3 * NN <= 128 ? 128 : 256));
-    static constexpr int SMEM = W_ALL + TC_STAGES * A_STAGE + 64;   // + mbarriers, TMEM address, abort flag
+    static constexpr int RAW = CPG * 3 * TC_PT * 16;         // cp.async slots: [channel][vector][thread]
+    static constexpr int SMEM = W_ALL + TC_STAGES * A_STAGE + RAW + 128;   // + mbarriers, TMEM address, abort flag
     // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
     // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
     static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NN >> 3) << 17) |
@@ -184,6 +195,10 @@ __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}" ::"r"(smem_addr(b)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
     uint32_t ok;
     asm volatile(
@@ -194,12 +209,20 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
     return ok != 0;
 }
 
-// wait for the completion of the phase with this parity; false after TC_WAIT_NS
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
+// Wait for the completion of the phase with this parity.  Returns false, with
+// the block's abort flag set, after TC_WAIT_NS or as soon as another thread has
+// set the flag, so one wait that runs out ends every role of the block.  With
+// abort_flag null only the time bound applies.
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     if (mbar_test(b, parity)) return true;
     const long long t0 = global_ns();
-    while (!mbar_test(b, parity))
-        if (global_ns() - t0 > TC_WAIT_NS) return false;
+    while (!mbar_test(b, parity)) {
+        if (abort_flag != nullptr && *abort_flag) return false;
+        if (global_ns() - t0 > TC_WAIT_NS) {
+            if (abort_flag != nullptr) *abort_flag = 1;
+            return false;
+        }
+    }
     return true;
 }
 
@@ -242,6 +265,113 @@ __device__ __forceinline__ uint32_t pack_f32bits(uint32_t re, uint32_t im) {
     return pack2(__uint_as_float(re), __uint_as_float(im));
 }
 
+// Where one thread's transport unit (site x, path p) reads: the neighbour y,
+// the FP16 link words (fetched into registers one stage ahead of their use) and
+// the boundary phase.  Its activation words go to shared memory by cp.async.
+struct TcUnit {
+    long y;
+    uint32_t link[6];
+    float ph;
+    int flags;   // bit 0 valid, bit 1 identity path, bit 2 link daggered
+};
+
+__device__ __forceinline__ void tc_locate(const PtcGeom& g, long x, int p, TcUnit& f) {
+    f.flags = 0;
+    if (p >= 9 || x >= g.V) return;
+    f.y = x;
+    f.ph = 1.f;
+    if (p == 0) {
+        f.flags = 3;
+        return;
+    }
+    int c[4];
+    site_coords(g, x, c[0], c[1], c[2], c[3]);
+    const int L[4] = {g.X, g.Y, g.Z, g.T};
+    const int mu = (p - 1) & 3;
+    const bool fwd = p <= 4;
+    int yc[4] = {c[0], c[1], c[2], c[3]};
+    if (fwd) {
+        yc[mu] = (c[mu] + 1 == L[mu]) ? 0 : c[mu] + 1;
+        if (mu == 3 && c[3] + 1 == g.T) f.ph = g.bc_t;
+    } else {
+        yc[mu] = (c[mu] == 0) ? L[mu] - 1 : c[mu] - 1;
+        if (mu == 3 && c[3] == 0) f.ph = g.bc_t;
+    }
+    f.y = (((long)yc[3] * g.Z + yc[2]) * g.Y + yc[1]) * g.X + yc[0];
+    const long ls = fwd ? x : f.y;                     // site that owns the link
+    const int* cs = fwd ? c : yc;
+    const int par = (cs[0] + cs[1] + cs[2] + cs[3]) & 1;
+    const unsigned int* base = reinterpret_cast<const unsigned int*>(g.gauge[par]);
+#pragma unroll
+    for (int k = 0; k < 6; ++k) f.link[k] = __ldg(base + (long)(mu * 6 + k) * g.vh + (ls >> 1));
+    f.flags = fwd ? 1 : 5;
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
+// SU(3) link of a located unit as 9 complex (row major), daggered for backward
+// paths and multiplied by the boundary phase
+__device__ __forceinline__ void tc_link(const TcUnit& f, cpx<float> (&u)[9]) {
+#pragma unroll
+    for (int k = 0; k < 6; ++k) {
+        const float2 h = h2f2<PF16>(f.link[k]);
+        u[k] = C(h.x, h.y);
+    }
+    su3_third_row(u);
+    if (f.flags & 4) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            u[4 * a] = cj(u[4 * a]);
+#pragma unroll
+            for (int b = a + 1; b < 3; ++b) {
+                const cpx<float> t = u[3 * a + b];
+                u[3 * a + b] = cj(u[3 * b + a]);
+                u[3 * b + a] = cj(t);
+            }
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 9; ++k) u[k] = f.ph * u[k];
+}
+
+// One channel of a unit: 12 activation words (complex (spin s, colour c) is
+// word 3 s + c) -> one 16-byte chunk per colour of the A images at img
+// (4 spins as BF16 (re, im) pairs), transported by u unless the path is the identity.
+template <int A_COL>
+__device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], bool identity, const cpx<float> (&u)[9],
+                                                     uint8_t* img) {
+    const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
+                            a[2].x, a[2].y, a[2].z, a[2].w};
+    if (identity) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(w[c], w[3 + c], w[6 + c], w[9 + c]);
+        return;
+    }
+    cpx<float> v[12];
+#pragma unroll
+    for (int e = 0; e < 12; ++e) {
+        const float2 h = h2f2<PB16>(w[e]);
+        v[e] = C(h.x, h.y);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        uint32_t wd[4];
+#pragma unroll
+        for (int s = 0; s < 4; ++s) {
+            cpx<float> t = u[3 * c] * v[3 * s];
+            cfma(t, u[3 * c + 1], v[3 * s + 1]);
+            cfma(t, u[3 * c + 2], v[3 * s + 2]);
+            wd[s] = pack2(t.re, t.im);
+        }
+        *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+    }
+}
+
 template <int CIN, int COUT>
 __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4* __restrict__ in,
                                                         uint4* __restrict__ out, const uint4* __restrict__ wimg,
@@ -250,8 +380,14 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* Wsm = smem;                                   // 9 paths of B images
     uint8_t* Asm = smem + S::W_ALL;                        // TC_STAGES stage buffers of A images
-    uint64_t* bar = reinterpret_cast<uint64_t*>(Asm + TC_STAGES * S::A_STAGE);   // [0, 1] stages, [2] drain
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 3);
+    uint8_t* Raw = Asm + TC_STAGES * S::A_STAGE;          // activation words of each thread's next stage
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Raw + S::RAW);
+    uint64_t* full = bar;                                  // [TC_STAGES] transport -> MMA
+    uint64_t* empty = bar + TC_STAGES;                     // [TC_STAGES] MMA -> transport
+    uint64_t* acc_full = bar + 2 * TC_STAGES;              // accumulators ready
+    uint64_t* acc_empty = acc_full + 1;                    // accumulators read back
+    uint64_t* drain = acc_full + 2;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(drain + 1);
     volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
@@ -265,7 +401,13 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         }
     }
     if (tid == 0) {
-        for (int k = 0; k < 3; ++k) mbar_init(bar + k, 1);
+        for (int k = 0; k < TC_STAGES; ++k) {
+            mbar_init(full + k, TC_PT);
+            mbar_init(empty + k, 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, TC_PT);
+        mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
@@ -281,78 +423,110 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = *tslot;
-
-    const int r = tid % TC_M, grp = tid / TC_M;            // transport: site r of the tile, site group
-    const int pi = grp / S::GPP;                           // path slot of this group within a stage
-    const int b0 = (grp % S::GPP) * S::CPG;                // first input channel of this thread
-    const uint32_t a_base = smem_addr(Asm), w_base = smem_addr(Wsm);
-    constexpr uint32_t SBO_A = 128 * S::KCH, SBO_W = 128 * S::KCH;
-    uint32_t u = 0;                                        // stages issued by this block so far
     bool ok = true;
-    // The abort flag is set only just before a barrier (a wait that ran out) and
-    // read only just after one, so every thread reads the same value.
-    bool stop = false;
 
-    for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const long x = tile * TC_M + r;
-        for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
-            const int buf = u % TC_STAGES;
-            // the MMAs that last read this buffer must be done before it is rewritten
-            if (u >= TC_STAGES && !mbar_wait(bar + buf, ((u / TC_STAGES) - 1) & 1)) {
-                ok = false;
-                *abort_flag = 1;
-            }
-            __syncthreads();
-            stop = *abort_flag != 0;
-            if (stop) break;
-            const int p = stg * S::NPS + pi;
-            if (p < 9 && x < g.V) {
-                uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * SBO_A + (r & 7) * 16;
-                auto sink = [&](int b, const cpx<float> (&w)[12]) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        *reinterpret_cast<uint4*>(img + c * S::A_COL + b * 128) =
-                            make_uint4(pack2(w[c].re, w[c].im), pack2(w[3 + c].re, w[3 + c].im),
-                                       pack2(w[6 + c].re, w[6 + c].im), pack2(w[9 + c].re, w[9 + c].im));
-                };
-                transport_channels<S::CPG>(g, in, x, p, b0, S::CPG, sink);
-            }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
+    if (warp == TC_PT / 32) {
+        // ---- MMA warp: one thread issues, the others wait at the final barrier
+        if (lane == 0) {
+            const uint32_t a_base = smem_addr(Asm), w_base = smem_addr(Wsm);
+            constexpr uint32_t SBO = 128 * S::KCH;
+            uint32_t u = 0, j = 0;
+            for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
+                if (j > 0 && !mbar_wait(acc_empty, (j - 1) & 1, abort_flag)) { ok = false; break; }
+                for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
+                    const int buf = u % TC_STAGES;
+                    if (!mbar_wait(full + buf, (u / TC_STAGES) & 1, abort_flag)) { ok = false; break; }
+                    tc_fence_after();
 #pragma unroll 1
-                for (int q = 0; q < S::NPS; ++q) {
-                    const int pp = stg * S::NPS + q;
-                    if (pp >= 9) break;
+                    for (int q = 0; q < S::NPS; ++q) {
+                        const int pp = stg * S::NPS + q;
+                        if (pp >= 9) break;
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
+                        for (int c = 0; c < 3; ++c)
 #pragma unroll
-                        for (int kk = 0; kk < S::KCH / 2; ++kk) {
-                            const uint32_t as = a_base + buf * S::A_STAGE + (q * 3 + c) * S::A_COL + kk * 256;
-                            const uint32_t ws = w_base + pp * S::W_PATH + kk * 256;
-                            tc_mma(tmem + c * S::NN, smem_desc(as, 128, SBO_A), smem_desc(ws, 128, SBO_W), S::IDESC,
-                                   (pp > 0 || kk > 0) ? 1u : 0u);
-                        }
+                            for (int kk = 0; kk < S::KCH / 2; ++kk) {
+                                const uint32_t as = a_base + buf * S::A_STAGE + (q * 3 + c) * S::A_COL + kk * 256;
+                                const uint32_t ws = w_base + pp * S::W_PATH + kk * 256;
+                                tc_mma(tmem + c * S::NN, smem_desc(as, 128, SBO), smem_desc(ws, 128, SBO), S::IDESC,
+                                       (pp > 0 || kk > 0) ? 1u : 0u);
+                            }
+                    }
+                    tc_commit(empty + buf);
                 }
-                tc_commit(bar + buf);
+                if (!ok) break;
+                tc_commit(acc_full);
             }
         }
-        if (stop) break;
-        // epilogue: all MMAs of the tile are behind the last commit
-        if (!mbar_wait(bar + (u - 1) % TC_STAGES, ((u - 1) / TC_STAGES) & 1)) {
-            ok = false;
-            *abort_flag = 1;
-        }
-        __syncthreads();
-        stop = *abort_flag != 0;
-        if (stop) break;
-        tc_fence_after();
         __syncwarp();
-        {
-            const int quarter = warp & 3, wg = warp >> 2;
+    } else {
+        // ---- transport warps
+        const int r = tid % TC_M, grp = tid / TC_M;        // site r of the tile, site group
+        const int pi = grp / S::GPP;                       // path slot of this group within a stage
+        const int b0 = (grp % S::GPP) * S::CPG;            // first input channel of this thread
+        const int quarter = warp & 3, wg = warp >> 2;      // epilogue: TMEM lane quarter, channel group
+        uint32_t u = 0, j = 0;
+        const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
+        const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
+        TcUnit nxt;
+        tc_locate(g, (long)blockIdx.x * TC_M + r, pi, nxt);
+        if (nxt.flags & 1) {
+#pragma unroll
+            for (int k = 0; k < S::CPG; ++k)
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    cp_async16(raw_base + (k * 3 + q) * TC_PT * 16, in + ((long)(b0 + k) * 3 + q) * g.V + nxt.y);
+        }
+        cp_async_commit();
+        for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+            for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
+                const int buf = u % TC_STAGES;
+                const TcUnit cur = nxt;
+                {   // this thread's next stage (possibly the next tile's first)
+                    const bool last = stg + 1 == S::NSTG;
+                    const long nt = last ? tile + gridDim.x : tile;
+                    const int np = (last ? 0 : (stg + 1) * S::NPS) + pi;
+                    nxt.flags = 0;
+                    if (nt < ntiles) tc_locate(g, nt * TC_M + r, np, nxt);
+                }
+                // every lane of a warp runs the same iterations, so the vote keeps the
+                // warp together on the way out and at the epilogue's aligned loads
+                const bool w = u < TC_STAGES || mbar_wait(empty + buf, ((u / TC_STAGES) - 1) & 1, abort_flag);
+                if (!__all_sync(0xffffffffu, w)) {
+                    ok = false;
+                    break;
+                }
+                cp_async_wait_all();
+                cpx<float> lk[9];
+                if ((cur.flags & 3) == 1) tc_link(cur, lk);
+                uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * (128 * S::KCH) +
+                               (r & 7) * 16;
+#pragma unroll
+                for (int k = 0; k < S::CPG; ++k) {
+                    if (cur.flags & 1) {
+                        uint4 a[3];
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) a[q] = rawp[(k * 3 + q) * TC_PT];
+                        tc_transport_channel<S::A_COL>(a, (cur.flags & 2) != 0, lk, img + (b0 + k) * 128);
+                    }
+                    // the slot's current words are consumed: bring the next stage's
+                    if (nxt.flags & 1) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q)
+                            cp_async16(raw_base + (k * 3 + q) * TC_PT * 16, in + ((long)(b0 + k) * 3 + q) * g.V + nxt.y);
+                    }
+                }
+                cp_async_commit();
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_arrive(full + buf);
+            }
+            if (!ok) break;
+            // epilogue: the accumulators of this tile
+            const bool w = mbar_wait(acc_full, j & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+            tc_fence_after();
             const long xo = tile * TC_M + 32 * quarter + lane;
-            constexpr int CPO = (COUT + 3) / 4;            // output channels per warp
+            constexpr int CPO = (COUT + TC_G - 1) / TC_G;  // output channels per warp
+            uint32_t wv[CPO][12];
 #pragma unroll
             for (int k = 0; k < CPO; ++k) {
                 const int a = wg * CPO + k;
@@ -363,32 +537,39 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     tmem_ld8(ta + S::NN, v1);
                     tmem_ld8(ta + 2 * S::NN, v2);
                     tmem_wait_ld(v0, v1, v2);
-                    if (xo < g.V) {
-                        // complex (s, c) at index 3 s + c; column 8 a + 2 s + ri of colour c
-                        uint32_t wv[12];
+                    // column 8 a + 2 s + ri of colour c -> complex (s, c), word 3 s + c
 #pragma unroll
-                        for (int s = 0; s < 4; ++s) {
-                            wv[3 * s + 0] = pack_f32bits(v0[2 * s], v0[2 * s + 1]);
-                            wv[3 * s + 1] = pack_f32bits(v1[2 * s], v1[2 * s + 1]);
-                            wv[3 * s + 2] = pack_f32bits(v2[2 * s], v2[2 * s + 1]);
-                        }
+                    for (int s = 0; s < 4; ++s) {
+                        wv[k][3 * s + 0] = pack_f32bits(v0[2 * s], v0[2 * s + 1]);
+                        wv[k][3 * s + 1] = pack_f32bits(v1[2 * s], v1[2 * s + 1]);
+                        wv[k][3 * s + 2] = pack_f32bits(v2[2 * s], v2[2 * s + 1]);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+            if (xo < g.V) {
+#pragma unroll
+                for (int k = 0; k < CPO; ++k) {
+                    const int a = wg * CPO + k;
+                    if (a < COUT) {
 #pragma unroll
                         for (int q = 0; q < 3; ++q)
                             out[((long)a * 3 + q) * g.V + xo] =
-                                make_uint4(wv[4 * q], wv[4 * q + 1], wv[4 * q + 2], wv[4 * q + 3]);
+                                make_uint4(wv[k][4 * q], wv[k][4 * q + 1], wv[k][4 * q + 2], wv[k][4 * q + 3]);
                     }
                 }
             }
         }
-        tc_fence_before();
-        __syncthreads();   // TMEM reads done before the next tile's first MMA overwrites D
     }
 
-    // drain: every MMA issued by this block completes before TMEM is released
+    // drain: every copy and MMA issued by this block completes (each wait bounded,
+    // also after an abort) before TMEM is released
+    cp_async_wait_all();
     __syncthreads();
-    if (tid == 0) {
-        tc_commit(bar + 2);
-        if (!mbar_wait(bar + 2, 0)) ok = false;
+    if (tid == TC_PT) {
+        tc_commit(drain);
+        if (!mbar_wait(drain, 0, nullptr)) ok = false;
     }
     if (!ok) atomicExch(err, 1);
     tc_fence_before();
