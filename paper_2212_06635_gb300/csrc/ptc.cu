@@ -265,45 +265,63 @@ __device__ __forceinline__ uint32_t pack_f32bits(uint32_t re, uint32_t im) {
     return pack2(__uint_as_float(re), __uint_as_float(im));
 }
 
-// Where one thread's transport unit (site x, path p) reads: the neighbour y,
-// the FP16 link words (fetched into registers one stage ahead of their use) and
-// the boundary phase.  Its activation words go to shared memory by cp.async.
-struct TcUnit {
-    long y;
-    uint32_t link[6];
-    float ph;
-    int flags;   // bit 0 valid, bit 1 identity path, bit 2 link daggered
+// Coordinates of one transport thread's site for the current tile (computed once
+// per tile; lattices of the layer kernel have fewer than 2^31 sites).
+struct TcSite {
+    int x, c[4];
+    bool valid;
 };
 
-__device__ __forceinline__ void tc_locate(const PtcGeom& g, long x, int p, TcUnit& f) {
+__device__ __forceinline__ TcSite tc_site(const PtcGeom& g, long xl) {
+    TcSite s;
+    s.valid = xl < g.V;
+    s.x = s.valid ? (int)xl : 0;
+    int r = s.x;
+    s.c[0] = r % g.X; r /= g.X;
+    s.c[1] = r % g.Y; r /= g.Y;
+    s.c[2] = r % g.Z;
+    s.c[3] = r / g.Z;
+    return s;
+}
+
+// Where one thread's transport unit (site, path p) reads: the neighbour y, the
+// FP16 link words (fetched into registers one stage ahead of their use) and the
+// boundary phase.  Its activation words go to shared memory by cp.async.
+struct TcUnit {
+    int y;
+    uint32_t link[6];
+    float ph;
+    int flags;   // bit 0 valid, bit 1 identity path, bit 2 link daggered (backward path)
+};
+
+__device__ __forceinline__ void tc_locate(const PtcGeom& g, const TcSite& s, int p, TcUnit& f) {
     f.flags = 0;
-    if (p >= 9 || x >= g.V) return;
-    f.y = x;
+    if (p >= 9 || !s.valid) return;
+    f.y = s.x;
     f.ph = 1.f;
     if (p == 0) {
         f.flags = 3;
         return;
     }
-    int c[4];
-    site_coords(g, x, c[0], c[1], c[2], c[3]);
-    const int L[4] = {g.X, g.Y, g.Z, g.T};
     const int mu = (p - 1) & 3;
     const bool fwd = p <= 4;
-    int yc[4] = {c[0], c[1], c[2], c[3]};
+    const int L = mu == 0 ? g.X : (mu == 1 ? g.Y : (mu == 2 ? g.Z : g.T));
+    const int st = mu == 0 ? 1 : (mu == 1 ? g.X : (mu == 2 ? g.X * g.Y : g.X * g.Y * g.Z));
+    const int cm = s.c[mu];
     if (fwd) {
-        yc[mu] = (c[mu] + 1 == L[mu]) ? 0 : c[mu] + 1;
-        if (mu == 3 && c[3] + 1 == g.T) f.ph = g.bc_t;
+        f.y = (cm + 1 == L) ? s.x - (L - 1) * st : s.x + st;
+        if (mu == 3 && cm + 1 == L) f.ph = g.bc_t;
     } else {
-        yc[mu] = (c[mu] == 0) ? L[mu] - 1 : c[mu] - 1;
-        if (mu == 3 && c[3] == 0) f.ph = g.bc_t;
+        f.y = (cm == 0) ? s.x + (L - 1) * st : s.x - st;
+        if (mu == 3 && cm == 0) f.ph = g.bc_t;
     }
-    f.y = (((long)yc[3] * g.Z + yc[2]) * g.Y + yc[1]) * g.X + yc[0];
-    const long ls = fwd ? x : f.y;                     // site that owns the link
-    const int* cs = fwd ? c : yc;
-    const int par = (cs[0] + cs[1] + cs[2] + cs[3]) & 1;
-    const unsigned int* base = reinterpret_cast<const unsigned int*>(g.gauge[par]);
+    // the link of a forward hop lives at the site, of a backward hop at the neighbour
+    // (opposite parity); checkerboard index = lexicographic index / 2
+    const int par = ((s.c[0] + s.c[1] + s.c[2] + s.c[3]) & 1) ^ (fwd ? 0 : 1);
+    const int owner = fwd ? s.x : f.y;
+    const unsigned int* base = reinterpret_cast<const unsigned int*>(g.gauge[par]) + (owner >> 1);
 #pragma unroll
-    for (int k = 0; k < 6; ++k) f.link[k] = __ldg(base + (long)(mu * 6 + k) * g.vh + (ls >> 1));
+    for (int k = 0; k < 6; ++k) f.link[k] = __ldg(base + (long)(mu * 6 + k) * g.vh);
     f.flags = fwd ? 1 : 5;
 }
 
@@ -313,8 +331,7 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
 
-// SU(3) link of a located unit as 9 complex (row major), daggered for backward
-// paths and multiplied by the boundary phase
+// SU(3) link of a located unit as 9 complex (row major; the third row rebuilt)
 __device__ __forceinline__ void tc_link(const TcUnit& f, cpx<float> (&u)[9]) {
 #pragma unroll
     for (int k = 0; k < 6; ++k) {
@@ -322,36 +339,16 @@ __device__ __forceinline__ void tc_link(const TcUnit& f, cpx<float> (&u)[9]) {
         u[k] = C(h.x, h.y);
     }
     su3_third_row(u);
-    if (f.flags & 4) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            u[4 * a] = cj(u[4 * a]);
-#pragma unroll
-            for (int b = a + 1; b < 3; ++b) {
-                const cpx<float> t = u[3 * a + b];
-                u[3 * a + b] = cj(u[3 * b + a]);
-                u[3 * b + a] = cj(t);
-            }
-        }
-    }
-#pragma unroll
-    for (int k = 0; k < 9; ++k) u[k] = f.ph * u[k];
 }
 
 // One channel of a unit: 12 activation words (complex (spin s, colour c) is
-// word 3 s + c) -> one 16-byte chunk per colour of the A images at img
-// (4 spins as BF16 (re, im) pairs), transported by u unless the path is the identity.
-template <int A_COL>
-__device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], bool identity, const cpx<float> (&u)[9],
+// word 3 s + c) -> one 16-byte chunk per colour of the A images at img (4 spins
+// as BF16 (re, im) pairs): t = ph U v, or ph U^dagger v for a backward path.
+template <int A_COL, bool DAG>
+__device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], const cpx<float> (&u)[9], float ph,
                                                      uint8_t* img) {
     const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
                             a[2].x, a[2].y, a[2].z, a[2].w};
-    if (identity) {
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-            *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(w[c], w[3 + c], w[6 + c], w[9 + c]);
-        return;
-    }
     cpx<float> v[12];
 #pragma unroll
     for (int e = 0; e < 12; ++e) {
@@ -363,13 +360,27 @@ __device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], bool i
         uint32_t wd[4];
 #pragma unroll
         for (int s = 0; s < 4; ++s) {
-            cpx<float> t = u[3 * c] * v[3 * s];
-            cfma(t, u[3 * c + 1], v[3 * s + 1]);
-            cfma(t, u[3 * c + 2], v[3 * s + 2]);
+            cpx<float> t = C(0.f, 0.f);
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (DAG) cfma_cj(t, u[3 * d + c], v[3 * s + d]);
+                else cfma(t, u[3 * c + d], v[3 * s + d]);
+            }
+            if (ph != 1.f) t = ph * t;
             wd[s] = pack2(t.re, t.im);
         }
         *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
+}
+
+// identity path: the words are only regrouped by colour
+template <int A_COL>
+__device__ __forceinline__ void tc_copy_channel(const uint4 (&a)[3], uint8_t* img) {
+    const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
+                            a[2].x, a[2].y, a[2].z, a[2].w};
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(w[c], w[3 + c], w[6 + c], w[9 + c]);
 }
 
 template <int CIN, int COUT>
@@ -467,8 +478,9 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         uint32_t u = 0, j = 0;
         const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
         const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
+        TcSite site = tc_site(g, (long)blockIdx.x * TC_M + r), nsite = site;
         TcUnit nxt;
-        tc_locate(g, (long)blockIdx.x * TC_M + r, pi, nxt);
+        tc_locate(g, site, pi, nxt);
         if (nxt.flags & 1) {
 #pragma unroll
             for (int k = 0; k < S::CPG; ++k)
@@ -485,8 +497,9 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     const bool last = stg + 1 == S::NSTG;
                     const long nt = last ? tile + gridDim.x : tile;
                     const int np = (last ? 0 : (stg + 1) * S::NPS) + pi;
+                    if (last) nsite = tc_site(g, nt * TC_M + r);
                     nxt.flags = 0;
-                    if (nt < ntiles) tc_locate(g, nt * TC_M + r, np, nxt);
+                    if (nt < ntiles) tc_locate(g, nsite, np, nxt);
                 }
                 // every lane of a warp runs the same iterations, so the vote keeps the
                 // warp together on the way out and at the epilogue's aligned loads
@@ -498,15 +511,19 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                 cp_async_wait_all();
                 cpx<float> lk[9];
                 if ((cur.flags & 3) == 1) tc_link(cur, lk);
+                const int kind = (cur.flags & 1) ? ((cur.flags & 2) ? 0 : ((cur.flags & 4) ? 2 : 1)) : -1;
                 uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * (128 * S::KCH) +
                                (r & 7) * 16;
 #pragma unroll
                 for (int k = 0; k < S::CPG; ++k) {
-                    if (cur.flags & 1) {
+                    if (kind >= 0) {
                         uint4 a[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) a[q] = rawp[(k * 3 + q) * TC_PT];
-                        tc_transport_channel<S::A_COL>(a, (cur.flags & 2) != 0, lk, img + (b0 + k) * 128);
+                        uint8_t* dst = img + (b0 + k) * 128;
+                        if (kind == 0) tc_copy_channel<S::A_COL>(a, dst);
+                        else if (kind == 1) tc_transport_channel<S::A_COL, false>(a, lk, cur.ph, dst);
+                        else tc_transport_channel<S::A_COL, true>(a, lk, cur.ph, dst);
                     }
                     // the slot's current words are consumed: bring the next stage's
                     if (nxt.flags & 1) {
@@ -897,6 +914,7 @@ static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const vo
                            cudaStream_t st) {
     using S = TcShape<CIN, COUT>;
     static_assert(S::SMEM <= 227 * 1024, "layer shared memory");
+    if (g.V >= (1L << 31)) return cudaErrorInvalidValue;   // site indices of the layer kernel are 32-bit
     static int cfg_dev = -1;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
