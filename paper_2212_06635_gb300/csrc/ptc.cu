@@ -124,12 +124,12 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 
 // ---------------------------------------------------------------------------
 // forward layer (also the input-gradient layer with adjoint weights) on the
-// fifth-generation tensor cores.  Per tile of TC_M = 128 sites and per path p,
-// colour c:  D_c[site][n] += A_{p,c}[site][k] * B_p[n][k]  (kind::f16, BF16 in,
-// FP32 accumulate in tensor memory), M = 128 sites, N = 8 COUT (re/im, spin,
-// output channel), K = 8 CIN (re/im, spin, input channel).
+// fifth-generation tensor cores.  Per tile of TC_SITES = 120 sites and per path
+// p, colour c:  D_c[site][n] += A_{p,c}[site][k] * B_p[n][k]  (kind::f16, BF16
+// in, FP32 accumulate in tensor memory), M = 128 rows (the last 8 unused),
+// N = 8 COUT (re/im, spin, output channel), K = 8 CIN (re/im, spin, input channel).
 //
-// Warp roles: 16 transport warps (4 threads per site) gather and transport the
+// Warp roles: 15 transport warps (4 threads per site) gather and transport the
 // input of one stage (one or more paths) into one of two stage buffers and
 // arrive on its "full" mbarrier.  Each thread's activation words for its next
 // stage are copied into a private shared-memory slot by cp.async (and its link
@@ -137,11 +137,12 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 // is issued once the channel's current words have been consumed.  One MMA warp waits for
 // "full", issues the stage's MMAs from one thread and commits them to the
 // buffer's "empty" mbarrier, so transport and MMAs overlap.  After a tile's last
-// stage the MMA warp commits to "acc_full"; the transport warps read the
-// accumulators back with tcgen05.ld (TMEM lane = site, so each thread owns one
-// site and writes its output vectors directly) and arrive on "acc_empty" before
-// the next tile's first MMA overwrites them.  The 9 paths' embedded weights (B)
-// stay resident in shared memory.
+// stage the MMA warp commits to "acc_full"; all 16 warps read the accumulators
+// back with tcgen05.ld (TMEM lane = site, so each thread owns one site and
+// writes its output vectors directly) and arrive on "acc_empty" before the next
+// tile's first MMA overwrites them.  The 9 paths' embedded weights (B) stay
+// resident in shared memory.  15 + 1 warps keep 128 registers per thread (4
+// warps per SM sub-partition), which a 17th warp would cut to 96.
 //
 // Shared-memory operand images are the canonical K-major layout without
 // swizzle: core matrices of 8 rows x 16 bytes (8 BF16 along K) stored as 128
@@ -149,10 +150,11 @@ __device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4
 // 8-row groups along M/N are SBO = 128 * KCH bytes apart (KCH 16-byte K chunks,
 // one per input channel: its 4 spins as (re, im) pairs).
 // ---------------------------------------------------------------------------
-constexpr int TC_M = 128;                  // sites per tile = MMA M = TMEM lanes
+constexpr int TC_M = 128;                  // MMA M = TMEM lanes
+constexpr int TC_SITES = 120;              // sites per tile (rows 120..127 of the MMA unused)
 constexpr int TC_G = 4;                    // site groups (transport threads per site)
-constexpr int TC_PT = TC_G * 128;          // transport threads
-constexpr int TC_BS = TC_PT + 32;          // + the MMA warp
+constexpr int TC_PT = TC_G * TC_SITES;     // transport threads (15 warps)
+constexpr int TC_BS = TC_PT + 32;          // + the MMA warp = 16 warps
 constexpr int TC_STAGES = 2;               // transport stage buffers
 constexpr long long TC_WAIT_NS = 1000000000LL;   // bound on every mbarrier wait (1 s)
 
@@ -209,6 +211,19 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
     return ok != 0;
 }
 
+// as mbar_test, but the thread may sleep up to TC_SUSPEND_NS for the phase, so a
+// waiting warp takes no issue slots from the working ones
+constexpr uint32_t TC_SUSPEND_NS = 20000;
+__device__ __forceinline__ bool mbar_test_sleep(uint64_t* b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(b)), "r"(parity), "r"(TC_SUSPEND_NS)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for the completion of the phase with this parity.  Returns false, with
 // the block's abort flag set, after TC_WAIT_NS or as soon as another thread has
 // set the flag, so one wait that runs out ends every role of the block.  With
@@ -216,7 +231,7 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
 __device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
     if (mbar_test(b, parity)) return true;
     const long long t0 = global_ns();
-    while (!mbar_test(b, parity)) {
+    while (!mbar_test_sleep(b, parity)) {
         if (abort_flag != nullptr && *abort_flag) return false;
         if (global_ns() - t0 > TC_WAIT_NS) {
             if (abort_flag != nullptr) *abort_flag = 1;
@@ -341,36 +356,63 @@ __device__ __forceinline__ void tc_link(const TcUnit& f, cpx<float> (&u)[9]) {
     su3_third_row(u);
 }
 
+// Link of a unit as broadcast pairs for paired FP32 FMAs: mr[c][d] = (Re M, Re M),
+// mi[c][d] = (Im M, Im M) with M = U, or U^dagger for a backward path.
+template <bool DAG>
+__device__ __forceinline__ void tc_link_pairs(const cpx<float> (&u)[9], float2 (&mr)[9], float2 (&mi)[9]) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            const cpx<float> e = DAG ? cj(u[3 * d + c]) : u[3 * c + d];
+            mr[3 * c + d] = make_float2(e.re, e.re);
+            mi[3 * c + d] = make_float2(e.im, e.im);
+        }
+}
+
 // One channel of a unit: 12 activation words (complex (spin s, colour c) is
 // word 3 s + c) -> one 16-byte chunk per colour of the A images at img (4 spins
-// as BF16 (re, im) pairs): t = ph U v, or ph U^dagger v for a backward path.
-template <int A_COL, bool DAG>
-__device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], const cpx<float> (&u)[9], float ph,
-                                                     uint8_t* img) {
+// as BF16 (re, im) pairs): t = ph M v.  Two spins share each paired FMA:
+//   Re t = sum_d Re M Re v + Im M (-Im v),  Im t = sum_d Re M Im v + Im M Re v,
+// each lane in the same order as the scalar form.
+template <int A_COL>
+__device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], const float2 (&mr)[9],
+                                                     const float2 (&mi)[9], float ph, uint8_t* img) {
     const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
                             a[2].x, a[2].y, a[2].z, a[2].w};
-    cpx<float> v[12];
+    uint32_t wd[3][4];
 #pragma unroll
-    for (int e = 0; e < 12; ++e) {
-        const float2 h = h2f2<PB16>(w[e]);
-        v[e] = C(h.x, h.y);
-    }
+    for (int h = 0; h < 2; ++h) {   // spins 2h, 2h + 1
+        float2 vr[3], vi[3], nvi[3];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        uint32_t wd[4];
+        for (int d = 0; d < 3; ++d) {
+            const uint32_t w0 = w[3 * (2 * h) + d], w1 = w[3 * (2 * h + 1) + d];
+            vr[d] = make_float2(__uint_as_float(w0 << 16), __uint_as_float(w1 << 16));
+            vi[d] = make_float2(__uint_as_float(w0 & 0xffff0000u), __uint_as_float(w1 & 0xffff0000u));
+            nvi[d] = make_float2(__uint_as_float((w0 ^ 0x80000000u) & 0xffff0000u),
+                                 __uint_as_float((w1 ^ 0x80000000u) & 0xffff0000u));
+        }
 #pragma unroll
-        for (int s = 0; s < 4; ++s) {
-            cpx<float> t = C(0.f, 0.f);
+        for (int c = 0; c < 3; ++c) {
+            float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
-                if (DAG) cfma_cj(t, u[3 * d + c], v[3 * s + d]);
-                else cfma(t, u[3 * c + d], v[3 * s + d]);
+                tr = __ffma2_rn(mr[3 * c + d], vr[d], tr);
+                tr = __ffma2_rn(mi[3 * c + d], nvi[d], tr);
+                ti = __ffma2_rn(mr[3 * c + d], vi[d], ti);
+                ti = __ffma2_rn(mi[3 * c + d], vr[d], ti);
             }
-            if (ph != 1.f) t = ph * t;
-            wd[s] = pack2(t.re, t.im);
+            if (ph != 1.f) {
+                tr = make_float2(ph * tr.x, ph * tr.y);
+                ti = make_float2(ph * ti.x, ph * ti.y);
+            }
+            wd[c][2 * h] = pack2(tr.x, ti.x);
+            wd[c][2 * h + 1] = pack2(tr.y, ti.y);
         }
-        *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
     }
+#pragma unroll
+    for (int c = 0; c < 3; ++c)
+        *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(wd[c][0], wd[c][1], wd[c][2], wd[c][3]);
 }
 
 // identity path: the words are only regrouped by colour
@@ -381,6 +423,57 @@ __device__ __forceinline__ void tc_copy_channel(const uint4 (&a)[3], uint8_t* im
 #pragma unroll
     for (int c = 0; c < 3; ++c)
         *reinterpret_cast<uint4*>(img + c * A_COL) = make_uint4(w[c], w[3 + c], w[6 + c], w[9 + c]);
+}
+
+// Epilogue of one tile, run by every warp of the block: wait for the tile's
+// accumulators, read this warp's TMEM lane quarter (rows 32 quarter + lane =
+// sites of the tile) for its output channels, release the accumulators and
+// store the BF16 output vectors.  False if the wait ran out (warp-uniform).
+template <typename S, int COUT>
+__device__ __forceinline__ bool tc_epilogue(uint32_t tmem, uint64_t* acc_full, uint64_t* acc_empty, uint32_t j,
+                                            volatile int* abort_flag, int quarter, int wg, int lane, long tile,
+                                            const PtcGeom& g, uint4* __restrict__ out) {
+    const bool w = mbar_wait(acc_full, j & 1, abort_flag);
+    if (!__all_sync(0xffffffffu, w)) return false;
+    tc_fence_after();
+    const int row = 32 * quarter + lane;
+    const long xo = tile * TC_SITES + row;
+    constexpr int CPO = (COUT + 3) / 4;                    // output channels per warp (4 warps per quarter)
+    uint32_t wv[CPO][12];
+#pragma unroll
+    for (int k = 0; k < CPO; ++k) {
+        const int a = wg * CPO + k;
+        if (a < COUT) {                                     // warp-uniform
+            uint32_t v0[8], v1[8], v2[8];
+            const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 8 * a;
+            tmem_ld8(ta, v0);
+            tmem_ld8(ta + S::NN, v1);
+            tmem_ld8(ta + 2 * S::NN, v2);
+            tmem_wait_ld(v0, v1, v2);
+            // column 8 a + 2 s + ri of colour c -> complex (s, c), word 3 s + c
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+                wv[k][3 * s + 0] = pack_f32bits(v0[2 * s], v0[2 * s + 1]);
+                wv[k][3 * s + 1] = pack_f32bits(v1[2 * s], v1[2 * s + 1]);
+                wv[k][3 * s + 2] = pack_f32bits(v2[2 * s], v2[2 * s + 1]);
+            }
+        }
+    }
+    tc_fence_before();
+    mbar_arrive(acc_empty);
+    if (row < TC_SITES && xo < g.V) {
+#pragma unroll
+        for (int k = 0; k < CPO; ++k) {
+            const int a = wg * CPO + k;
+            if (a < COUT) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    out[((long)a * 3 + q) * g.V + xo] =
+                        make_uint4(wv[k][4 * q], wv[k][4 * q + 1], wv[k][4 * q + 2], wv[k][4 * q + 3]);
+            }
+        }
+    }
+    return true;
 }
 
 template <int CIN, int COUT>
@@ -417,7 +510,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
             mbar_init(empty + k, 1);
         }
         mbar_init(acc_full, 1);
-        mbar_init(acc_empty, TC_PT);
+        mbar_init(acc_empty, TC_BS);
         mbar_init(drain, 1);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -436,15 +529,16 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
     const uint32_t tmem = *tslot;
     bool ok = true;
 
+    const int quarter = warp & 3, wg = warp >> 2;          // epilogue: TMEM lane quarter, channel group
     if (warp == TC_PT / 32) {
-        // ---- MMA warp: one thread issues, the others wait at the final barrier
-        if (lane == 0) {
-            const uint32_t a_base = smem_addr(Asm), w_base = smem_addr(Wsm);
-            constexpr uint32_t SBO = 128 * S::KCH;
-            uint32_t u = 0, j = 0;
-            for (long tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x, ++j) {
-                if (j > 0 && !mbar_wait(acc_empty, (j - 1) & 1, abort_flag)) { ok = false; break; }
-                for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
+        // ---- MMA warp: one thread issues; the whole warp joins each epilogue
+        const uint32_t a_base = smem_addr(Asm), w_base = smem_addr(Wsm);
+        constexpr uint32_t SBO = 128 * S::KCH;
+        uint32_t u = 0, j = 0;
+        for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
+            if (lane == 0) {
+                if (j > 0 && !mbar_wait(acc_empty, (j - 1) & 1, abort_flag)) ok = false;
+                for (int stg = 0; stg < S::NSTG && ok; ++stg, ++u) {
                     const int buf = u % TC_STAGES;
                     if (!mbar_wait(full + buf, (u / TC_STAGES) & 1, abort_flag)) { ok = false; break; }
                     tc_fence_after();
@@ -464,21 +558,24 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     }
                     tc_commit(empty + buf);
                 }
-                if (!ok) break;
-                tc_commit(acc_full);
+                if (ok) tc_commit(acc_full);
+            }
+            ok = __shfl_sync(0xffffffffu, ok, 0);
+            if (!ok) break;
+            if (!tc_epilogue<S, COUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
+                ok = false;
+                break;
             }
         }
-        __syncwarp();
     } else {
         // ---- transport warps
-        const int r = tid % TC_M, grp = tid / TC_M;        // site r of the tile, site group
+        const int r = tid % TC_SITES, grp = tid / TC_SITES;   // site r of the tile, site group
         const int pi = grp / S::GPP;                       // path slot of this group within a stage
         const int b0 = (grp % S::GPP) * S::CPG;            // first input channel of this thread
-        const int quarter = warp & 3, wg = warp >> 2;      // epilogue: TMEM lane quarter, channel group
         uint32_t u = 0, j = 0;
         const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
         const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
-        TcSite site = tc_site(g, (long)blockIdx.x * TC_M + r), nsite = site;
+        TcSite site = tc_site(g, (long)blockIdx.x * TC_SITES + r), nsite = site;
         TcUnit nxt;
         tc_locate(g, site, pi, nxt);
         if (nxt.flags & 1) {
@@ -497,7 +594,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     const bool last = stg + 1 == S::NSTG;
                     const long nt = last ? tile + gridDim.x : tile;
                     const int np = (last ? 0 : (stg + 1) * S::NPS) + pi;
-                    if (last) nsite = tc_site(g, nt * TC_M + r);
+                    if (last) nsite = tc_site(g, nt * TC_SITES + r);
                     nxt.flags = 0;
                     if (nt < ntiles) tc_locate(g, nsite, np, nxt);
                 }
@@ -509,21 +606,25 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     break;
                 }
                 cp_async_wait_all();
-                cpx<float> lk[9];
-                if ((cur.flags & 3) == 1) tc_link(cur, lk);
-                const int kind = (cur.flags & 1) ? ((cur.flags & 2) ? 0 : ((cur.flags & 4) ? 2 : 1)) : -1;
+                float2 mr[9], mi[9];
+                if ((cur.flags & 3) == 1) {
+                    cpx<float> lk[9];
+                    tc_link(cur, lk);
+                    if (cur.flags & 4) tc_link_pairs<true>(lk, mr, mi);
+                    else tc_link_pairs<false>(lk, mr, mi);
+                }
+                const bool copy = (cur.flags & 2) != 0;
                 uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * (128 * S::KCH) +
                                (r & 7) * 16;
 #pragma unroll
                 for (int k = 0; k < S::CPG; ++k) {
-                    if (kind >= 0) {
+                    if (cur.flags & 1) {
                         uint4 a[3];
 #pragma unroll
                         for (int q = 0; q < 3; ++q) a[q] = rawp[(k * 3 + q) * TC_PT];
                         uint8_t* dst = img + (b0 + k) * 128;
-                        if (kind == 0) tc_copy_channel<S::A_COL>(a, dst);
-                        else if (kind == 1) tc_transport_channel<S::A_COL, false>(a, lk, cur.ph, dst);
-                        else tc_transport_channel<S::A_COL, true>(a, lk, cur.ph, dst);
+                        if (copy) tc_copy_channel<S::A_COL>(a, dst);
+                        else tc_transport_channel<S::A_COL>(a, mr, mi, cur.ph, dst);
                     }
                     // the slot's current words are consumed: bring the next stage's
                     if (nxt.flags & 1) {
@@ -537,45 +638,9 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                 mbar_arrive(full + buf);
             }
             if (!ok) break;
-            // epilogue: the accumulators of this tile
-            const bool w = mbar_wait(acc_full, j & 1, abort_flag);
-            if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
-            tc_fence_after();
-            const long xo = tile * TC_M + 32 * quarter + lane;
-            constexpr int CPO = (COUT + TC_G - 1) / TC_G;  // output channels per warp
-            uint32_t wv[CPO][12];
-#pragma unroll
-            for (int k = 0; k < CPO; ++k) {
-                const int a = wg * CPO + k;
-                if (a < COUT) {                             // warp-uniform
-                    uint32_t v0[8], v1[8], v2[8];
-                    const uint32_t ta = tmem + ((uint32_t)(32 * quarter) << 16) + 8 * a;
-                    tmem_ld8(ta, v0);
-                    tmem_ld8(ta + S::NN, v1);
-                    tmem_ld8(ta + 2 * S::NN, v2);
-                    tmem_wait_ld(v0, v1, v2);
-                    // column 8 a + 2 s + ri of colour c -> complex (s, c), word 3 s + c
-#pragma unroll
-                    for (int s = 0; s < 4; ++s) {
-                        wv[k][3 * s + 0] = pack_f32bits(v0[2 * s], v0[2 * s + 1]);
-                        wv[k][3 * s + 1] = pack_f32bits(v1[2 * s], v1[2 * s + 1]);
-                        wv[k][3 * s + 2] = pack_f32bits(v2[2 * s], v2[2 * s + 1]);
-                    }
-                }
-            }
-            tc_fence_before();
-            mbar_arrive(acc_empty);
-            if (xo < g.V) {
-#pragma unroll
-                for (int k = 0; k < CPO; ++k) {
-                    const int a = wg * CPO + k;
-                    if (a < COUT) {
-#pragma unroll
-                        for (int q = 0; q < 3; ++q)
-                            out[((long)a * 3 + q) * g.V + xo] =
-                                make_uint4(wv[k][4 * q], wv[k][4 * q + 1], wv[k][4 * q + 2], wv[k][4 * q + 3]);
-                    }
-                }
+            if (!tc_epilogue<S, COUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
+                ok = false;
+                break;
             }
         }
     }
@@ -924,7 +989,7 @@ static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const vo
         if (e != cudaSuccess) return e;
         cfg_dev = dev;
     }
-    const long ntiles = (g.V + TC_M - 1) / TC_M;
+    const long ntiles = (g.V + TC_SITES - 1) / TC_SITES;
     const long grid = std::min<long>(ntiles, nsm);
     ptc_layer_tc<CIN, COUT><<<(unsigned)grid, TC_BS, S::SMEM, st>>>(
         g, reinterpret_cast<const uint4*>(in), reinterpret_cast<uint4*>(out), reinterpret_cast<const uint4*>(w),
