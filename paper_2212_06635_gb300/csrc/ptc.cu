@@ -28,7 +28,13 @@ namespace tmk {
 
 __device__ __forceinline__ float bf(uint16_t v) { return __bfloat162float(__ushort_as_bfloat16(v)); }
 __device__ __forceinline__ uint16_t fb(float v) { return __bfloat16_as_ushort(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ uint32_t pack2(float lo, float hi) { return (uint32_t)fb(lo) | ((uint32_t)fb(hi) << 16); }
+// two FP32 values rounded to nearest-even BF16 in one 32-bit word (lo in the low half)
+__device__ __forceinline__ uint32_t pack2(float lo, float hi) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    uint32_t w;
+    memcpy(&w, &h, 4);
+    return w;
+}
 
 __device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
                                          uint32_t b0, uint32_t b1) {
