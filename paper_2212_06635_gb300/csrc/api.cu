@@ -1403,7 +1403,6 @@ struct tm_ptc {
     void* act[9] = {};      // activations per layer boundary, BF16 [ch][3][V] uint4
     void* del[2] = {};      // back-propagated deltas (8 channels)
     float* wpart = nullptr; // weight-gradient partials
-    int nchunk = 0;
     double* dpart = nullptr;
     double* dscal = nullptr;   // [0] ||e||^2, [1] loss sum, [2..] scratch
     double* hscal = nullptr;
@@ -1452,8 +1451,7 @@ extern "C" tm_status tm_ptc_create(tm_ptc** out, int nlayers, const int* channel
         CK(cudaMalloc(&n->wf[l], 2 * 9 * 64 * 64));
         CK(cudaMalloc(&n->wa[l], 2 * 9 * 64 * 64));
     }
-    n->nchunk = 4 * n->nsm;
-    CK(cudaMalloc(&n->wpart, sizeof(float) * 9 * 4096 * n->nchunk));
+    CK(cudaMalloc(&n->wpart, sizeof(float) * 9 * 4096 * n->nsm));
     CK(cudaMalloc(&n->dscal, sizeof(double) * 8));
     CK(cudaMallocHost(&n->hscal, sizeof(double) * 8));
     CK(cudaMalloc(&n->derr, sizeof(int)));
@@ -1611,7 +1609,8 @@ static tm_status ptc_backward(tm_ptc* n, tm_ctx* c, const void* e, float scale, 
     CK(launch_ptc_loss_delta(n->act[n->L], e, n->del[0], g, n->dscal + 0, n->dpart, n->dscal + 1, st));
     int cur = 0;
     for (int l = n->L - 1; l >= 0; --l) {
-        CK(launch_ptc_wgrad(n->ch[l], n->ch[l + 1], g, n->act[l], n->del[cur], n->wpart, n->nchunk, n->G[l], scale, st));
+        CK(launch_ptc_wgrad(n->ch[l], n->ch[l + 1], g, n->act[l], n->del[cur], n->wpart, n->nsm, n->G[l], scale,
+                            n->derr, st));
         if (l > 0) {
             CK(launch_ptc_layer(n->ch[l + 1], n->ch[l], g, n->del[cur], n->del[1 - cur], n->wa[l], n->nsm, n->derr,
                                 st));

@@ -13,9 +13,8 @@
 //   A_p = [[Re W, -Im W], [Im W, Re W]] (BF16), V_p = T_p in (BF16), FP32 accumulate.
 // The transport (gather of neighbour activations, SU(3) multiply) fills V_p in
 // shared memory; the mixing runs on the tcgen05 tensor cores with the
-// accumulators in tensor memory (ptc_layer_tc).  The weight gradient uses
-// mma.sync m16n8k16 (BF16 in, FP32 accumulate) with channel counts below 8
-// zero-padded.  Activations are BF16, layout
+// accumulators in tensor memory (ptc_layer_tc), and so does the weight gradient
+// (ptc_wgrad_tc).  Activations are BF16, layout
 // [channel][3 x 16-B vectors of 4 complex (spin, colour)][V] in lexicographic site
 // order.  The input gradient of a layer is the same layer run with the adjoint
 // weights W'_p = (W_{rev p})^H (T_p^dag = T_{rev p}); the weight gradient is the
@@ -36,47 +35,12 @@ __device__ __forceinline__ uint32_t pack2(float lo, float hi) {
     return w;
 }
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                         uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ void site_coords(const PtcGeom& g, long x, int& cx, int& cy, int& cz, int& ct) {
     long r = x;
     cx = (int)(r % g.X); r /= g.X;
     cy = (int)(r % g.Y); r /= g.Y;
     cz = (int)(r % g.Z);
     ct = (int)(r / g.Z);
-}
-
-// neighbour site, link and phase of path p at lex site x; dag = use U^dagger
-__device__ __forceinline__ long path_site(const PtcGeom& g, long x, int p, cpx<float> (&u)[9], bool& dag,
-                                          float& ph) {
-    int c[4];
-    site_coords(g, x, c[0], c[1], c[2], c[3]);
-    const int L[4] = {g.X, g.Y, g.Z, g.T};
-    const int mu = (p - 1) & 3;
-    const bool fwd = p <= 4;
-    ph = 1.f;
-    int y[4] = {c[0], c[1], c[2], c[3]};
-    if (fwd) {
-        y[mu] = (c[mu] + 1 == L[mu]) ? 0 : c[mu] + 1;
-        if (mu == 3 && c[3] + 1 == g.T) ph = g.bc_t;
-    } else {
-        y[mu] = (c[mu] == 0) ? L[mu] - 1 : c[mu] - 1;
-        if (mu == 3 && c[3] == 0) ph = g.bc_t;
-    }
-    const long ly = (((long)y[3] * g.Z + y[2]) * g.Y + y[1]) * g.X + y[0];
-    const long ls = fwd ? x : ly;                       // site that owns the link
-    const int* cs = fwd ? c : y;
-    const int par = (cs[0] + cs[1] + cs[2] + cs[3]) & 1;
-    load_link<PF16>(g.gauge[par], g.vh, mu, ls >> 1, u);
-    dag = !fwd;
-    return ly;
 }
 
 // 12 complex (spin, colour) of channel b at site y
@@ -87,44 +51,6 @@ __device__ __forceinline__ void act_load(const uint4* a, long V, int b, long y, 
         const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[4 * q + k] = C(bf((uint16_t)(ws[k] & 0xffffu)), bf((uint16_t)(ws[k] >> 16)));
-    }
-}
-
-// Transport channels [b0, b0 + n) of `in` along path p to site x: the link and
-// the neighbour index are computed once for the whole channel group; each
-// transported 12-complex (spin, colour) spinor is handed to sink(b, w).
-template <int NMAX, typename Sink>
-__device__ __forceinline__ void transport_channels(const PtcGeom& g, const uint4* in, long x, int p, int b0,
-                                                   int n, Sink&& sink) {
-    cpx<float> u[9];
-    bool dag = false;
-    float ph = 1.f;
-    long y = x;
-    if (p != 0) y = path_site(g, x, p, u, dag, ph);
-#pragma unroll
-    for (int k = 0; k < NMAX; ++k) {
-        if (k >= n) break;
-        const int b = b0 + k;
-        cpx<float> v[12], w[12];
-        act_load(in, g.V, b, y, v);
-        if (p == 0) {
-#pragma unroll
-            for (int q = 0; q < 12; ++q) w[q] = v[q];
-        } else {
-#pragma unroll
-            for (int sp = 0; sp < 4; ++sp)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    cpx<float> t = C(0.f, 0.f);
-#pragma unroll
-                    for (int d = 0; d < 3; ++d) {
-                        if (dag) cfma_cj(t, u[3 * d + c], v[3 * sp + d]);
-                        else cfma(t, u[3 * c + d], v[3 * sp + d]);
-                    }
-                    w[3 * sp + c] = ph * t;
-                }
-        }
-        sink(b, w);
     }
 }
 
@@ -671,102 +597,302 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
 }
 
 // ---------------------------------------------------------------------------
-// weight gradient: Q_p[m][k] = sum_n D[m][n] V_p[k][n] over all (site, colour)
-// columns n; D = [Re delta; Im delta] (64 rows), V_p = [Re T_p in; Im T_p in].
-// Block (p, chunk) accumulates over its range of tiles and writes a partial.
+// weight gradient on the tensor cores:
+//   Q_p[m][n] = sum_{x, c} V_p[m](x, c) Delta[n](x, c),
+// V_p = T_p in (rows m = 8 b + 2 t + ri: input channel b, spin t, re/im) and
+// Delta the back-propagated delta (rows n = 8 a + 2 s + ri), the reduction over
+// the (colour, site) pairs of the block's sites.  One MMA (M = 128) stacks the
+// rows of PPM = 16 / CIN paths; NG = ceil(9 / PPM) accumulators of N = 8 COUT
+// columns stay in tensor memory for the whole kernel.  A stage is (block of 32
+// sites, path group): 16 transport warps, one (site, path, channel) unit per
+// thread, write its A image; in a block's first stage the delta of the 32 sites
+// is written too (B image, double-buffered by site block).  One MMA warp issues
+// 6 MMAs of K = 16 per stage.  Both images are MN-major without swizzle: a
+// 16-byte chunk holds 8 consecutive rows of one K index (k = 32 c + j), core
+// matrices (8 K x 8 rows) of 128 bytes, LBO = 128 bytes between K groups, SBO =
+// 12 * 128 bytes between 8-row groups.  At the end every warp reads its TMEM
+// lane quarter and writes the block's partial Q_p.
 // ---------------------------------------------------------------------------
-constexpr int LDG = 52;   // padded row length in words (104 bf16) for 96 columns
+constexpr int WG_S = 32;                   // sites per stage
+constexpr int WG_K = 3 * WG_S;             // MMA K per stage (colour, site)
+constexpr int WG_PT = 512;                 // transport threads (16 warps)
+constexpr int WG_BS = WG_PT + 32;          // + the MMA warp
+constexpr int WG_SBO = (WG_K / 8) * 128;   // bytes between 8-row groups of an image
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(PTC_BS) ptc_wgrad_kernel(PtcGeom g, const uint4* __restrict__ in,
-                                                          const uint4* __restrict__ delta, float* partial,
-                                                          long ntiles, int nchunk) {
-    __shared__ __align__(16) uint32_t VT[64 * LDG];
-    __shared__ __align__(16) uint32_t DS[64 * LDG];
-    const int p = blockIdx.x / nchunk, chunk = blockIdx.x % nchunk;
-    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, gq = lane >> 2, tq = lane & 3;
-    uint16_t* VT16 = reinterpret_cast<uint16_t*>(VT);
-    uint16_t* DS16 = reinterpret_cast<uint16_t*>(DS);
-    for (int e = tid; e < 64 * LDG; e += PTC_BS) { VT[e] = 0u; DS[e] = 0u; }
-    __syncthreads();
-    float acc[8][4];
+struct WgShape {
+    static constexpr int PPM = 16 / CIN;                      // paths stacked per MMA
+    static constexpr int NG = (9 + PPM - 1) / PPM;            // MMA groups (accumulators)
+    static constexpr int NN = 8 * COUT < 16 ? 16 : 8 * COUT;  // N
+    static constexpr int A_IMG = 128 / 8 * WG_SBO;            // bytes of one A image (128 rows)
+    static constexpr int B_IMG = NN / 8 * WG_SBO;             // bytes of one B image
+    static constexpr int RAW = 3 * WG_PT * 16;                // cp.async slots [vector][thread]
+    static constexpr int COLS = NG * NN;
+    static constexpr int TMEM_COLS = COLS <= 32 ? 32 : (COLS <= 64 ? 64 : (COLS <= 128 ? 128 : (COLS <= 256 ? 256 : 512)));
+    static constexpr int SMEM = 2 * A_IMG + 2 * B_IMG + RAW + 128;
+    // kind::f16: D F32, A and B BF16, both MN-major (bits 15, 16), N >> 3, M >> 4
+    static constexpr uint32_t IDESC = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                      ((uint32_t)(NN >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+};
+
+__device__ __forceinline__ void tmem_wait_ld1(uint32_t (&a)[8]) {
+    asm volatile("tcgen05.wait::ld.sync.aligned;"
+                 : "+r"(a[0]), "+r"(a[1]), "+r"(a[2]), "+r"(a[3]), "+r"(a[4]), "+r"(a[5]), "+r"(a[6]), "+r"(a[7])
+                 :
+                 : "memory");
+}
+
+// One (site, path, channel) unit: transport (or copy for the identity path) and
+// write its 8 rows (2 t + ri) for each colour's K index as a 16-byte BF16 chunk.
+__device__ __forceinline__ void wg_transport_unit(const uint4 (&a)[3], const float2 (&mr)[9], const float2 (&mi)[9],
+                                                  float ph, bool copy, uint8_t* img, int j) {
+    const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
+                            a[2].x, a[2].y, a[2].z, a[2].w};
+    uint32_t wd[3][4];   // [colour][spin]: (re, im) BF16
+    if (copy) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a)
+        for (int c = 0; c < 3; ++c)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[a][c] = 0.f;
-    const long per = (ntiles + nchunk - 1) / nchunk;
-    const long t0 = chunk * per, t1 = min(ntiles, t0 + per);
-    for (long tile = t0; tile < t1; ++tile) {
-        const long x0 = tile * PTC_TILE;
-        {
-            constexpr int CPG = (CIN + 3) / 4;   // channels per transport group (4 groups of 32 sites)
-            const int j = tid % PTC_TILE, grp = tid / PTC_TILE;
-            const long x = x0 + j;
-            const int b0 = grp * CPG, nb = min(CPG, CIN - b0);
-            auto sink = [&](int b, const cpx<float> (&w)[12]) {
+            for (int s = 0; s < 4; ++s) wd[c][s] = w[3 * s + c];
+    } else {
 #pragma unroll
-                for (int sp = 0; sp < 4; ++sp)
+        for (int h = 0; h < 2; ++h) {
+            float2 vr[3], vi[3], nvi[3];
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        VT16[(4 * b + sp) * 2 * LDG + 3 * j + c] = fb(w[3 * sp + c].re);
-                        VT16[(32 + 4 * b + sp) * 2 * LDG + 3 * j + c] = fb(w[3 * sp + c].im);
-                    }
-            };
-            if (nb > 0) {
-                if (x < g.V) {
-                    transport_channels<CPG>(g, in, x, p, b0, nb, sink);
-                } else {
-                    cpx<float> z[12];
+            for (int d = 0; d < 3; ++d) {
+                const uint32_t w0 = w[3 * (2 * h) + d], w1 = w[3 * (2 * h + 1) + d];
+                vr[d] = make_float2(__uint_as_float(w0 << 16), __uint_as_float(w1 << 16));
+                vi[d] = make_float2(__uint_as_float(w0 & 0xffff0000u), __uint_as_float(w1 & 0xffff0000u));
+                nvi[d] = make_float2(__uint_as_float((w0 ^ 0x80000000u) & 0xffff0000u),
+                                     __uint_as_float((w1 ^ 0x80000000u) & 0xffff0000u));
+            }
 #pragma unroll
-                    for (int q = 0; q < 12; ++q) z[q] = C(0.f, 0.f);
-                    for (int k = 0; k < nb; ++k) sink(b0 + k, z);
+            for (int c = 0; c < 3; ++c) {
+                float2 tr = make_float2(0.f, 0.f), ti = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    tr = __ffma2_rn(mr[3 * c + d], vr[d], tr);
+                    tr = __ffma2_rn(mi[3 * c + d], nvi[d], tr);
+                    ti = __ffma2_rn(mr[3 * c + d], vi[d], ti);
+                    ti = __ffma2_rn(mi[3 * c + d], vr[d], ti);
                 }
-            }
-        }
-        for (int it = tid; it < PTC_TILE * COUT; it += PTC_BS) {
-            const int j = it % PTC_TILE, a = it / PTC_TILE;
-            const long x = x0 + j;
-            cpx<float> d[12];
-            if (x < g.V) act_load(delta, g.V, a, x, d);
-            else {
-#pragma unroll
-                for (int q = 0; q < 12; ++q) d[q] = C(0.f, 0.f);
-            }
-#pragma unroll
-            for (int s = 0; s < 4; ++s)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    DS16[(4 * a + s) * 2 * LDG + 3 * j + c] = fb(d[3 * s + c].re);
-                    DS16[(32 + 4 * a + s) * 2 * LDG + 3 * j + c] = fb(d[3 * s + c].im);
+                if (ph != 1.f) {
+                    tr = make_float2(ph * tr.x, ph * tr.y);
+                    ti = make_float2(ph * ti.x, ph * ti.y);
                 }
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < 6; ++kk) {
-            const uint32_t* ar = DS + (16 * warp + gq) * LDG + 8 * kk + tq;
-            const uint32_t a0 = ar[0], a1 = ar[8 * LDG], a2 = ar[4], a3 = ar[8 * LDG + 4];
-#pragma unroll
-            for (int nt = 0; nt < 8; ++nt) {
-                const uint32_t* br = VT + (8 * nt + gq) * LDG + 8 * kk + tq;
-                mma_bf16(acc[nt], a0, a1, a2, a3, br[0], br[4]);
+                wd[c][2 * h] = pack2(tr.x, ti.x);
+                wd[c][2 * h + 1] = pack2(tr.y, ti.y);
             }
         }
-        __syncthreads();
     }
-    float* dst = partial + (size_t)blockIdx.x * 4096;
+    // K index k = 32 c + j: core matrix k / 8 (LBO = 128), row k % 8 (16 bytes)
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            const int m = 16 * warp + gq + 8 * (r >> 1);
-            const int k = 8 * nt + 2 * tq + (r & 1);
-            dst[m * 64 + k] = acc[nt][r];
+    for (int c = 0; c < 3; ++c)
+        *reinterpret_cast<uint4*>(img + ((WG_S * c + j) >> 3) * 128 + (j & 7) * 16) =
+            make_uint4(wd[c][0], wd[c][1], wd[c][2], wd[c][3]);
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4* __restrict__ in,
+                                                        const uint4* __restrict__ delta, float* __restrict__ partial,
+                                                        long nsb, int* err) {
+    using S = WgShape<CIN, COUT>;
+    extern __shared__ __align__(1024) uint8_t smem[];
+    uint8_t* Asm = smem;                                    // 2 A images
+    uint8_t* Bsm = smem + 2 * S::A_IMG;                     // 2 B images (by site-block parity)
+    uint8_t* Raw = Bsm + 2 * S::B_IMG;
+    uint64_t* bar = reinterpret_cast<uint64_t*>(Raw + S::RAW);
+    uint64_t* full = bar;                                   // [2]
+    uint64_t* empty = bar + 2;                              // [2]
+    uint64_t* acc_full = bar + 4;   // every MMA of the block done
+    uint64_t* drain = bar + 5;
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 6);
+    volatile int* abort_flag = reinterpret_cast<volatile int*>(tslot + 1);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    // rows of absent paths (p >= 9) and the B rows beyond 8 COUT must read as zero
+    for (int e = tid; e < (2 * S::A_IMG + 2 * S::B_IMG) / 16; e += WG_BS)
+        reinterpret_cast<uint4*>(smem)[e] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid == 0) {
+        for (int k = 0; k < 2; ++k) {
+            mbar_init(full + k, WG_PT);
+            mbar_init(empty + k, 1);
         }
+        mbar_init(acc_full, 1);
+        mbar_init(drain, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        __syncwarp();
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(tslot)),
+                     "r"((uint32_t)S::TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    bool ok = true;
+    // this block's site blocks (every block gets at least one: gridDim.x <= nsb)
+    const long sb0 = blockIdx.x * nsb / gridDim.x, sb1 = (blockIdx.x + 1) * nsb / gridDim.x;
+    const int nst = (int)(sb1 > sb0 ? (sb1 - sb0) * S::NG : 0);
+
+    if (warp == WG_PT / 32) {
+        // ---- MMA warp
+        if (lane == 0) {
+            const uint32_t a_base = smem_addr(Asm), b_base = smem_addr(Bsm);
+            for (int u = 0; u < nst; ++u) {
+                const int buf = u & 1, grp = u % S::NG, sbi = u / S::NG;
+                if (!mbar_wait(full + buf, (u >> 1) & 1, abort_flag)) { ok = false; break; }
+                tc_fence_after();
+#pragma unroll
+                for (int kk = 0; kk < WG_K / 16; ++kk) {
+                    const uint32_t as = a_base + buf * S::A_IMG + kk * 256;
+                    const uint32_t bs = b_base + (sbi & 1) * S::B_IMG + kk * 256;
+                    tc_mma(tmem + grp * S::NN, smem_desc(as, 128, WG_SBO), smem_desc(bs, 128, WG_SBO), S::IDESC,
+                           (sbi > 0 || kk > 0) ? 1u : 0u);
+                }
+                tc_commit(empty + buf);
+            }
+            if (ok) tc_commit(acc_full);
+        }
+        ok = __shfl_sync(0xffffffffu, ok, 0);
+    } else {
+        // ---- transport warps: unit (site j, path slot ps, channel b)
+        const int j = tid % WG_S, unit = tid / WG_S;        // unit < 16
+        const int ps = unit / CIN, b = unit % CIN;
+        const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
+        const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
+        auto locate = [&](int u, TcUnit& f) {
+            f.flags = 0;
+            if (u >= nst) return;
+            const int grp = u % S::NG;
+            const long sb = sb0 + u / S::NG;
+            tc_locate(g, tc_site(g, sb * WG_S + j), grp * S::PPM + ps, f);
+        };
+        TcUnit nxt;
+        locate(0, nxt);
+        if (nxt.flags & 1) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) cp_async16(raw_base + q * WG_PT * 16, in + ((long)b * 3 + q) * g.V + nxt.y);
+        }
+        cp_async_commit();
+        for (int u = 0; u < nst; ++u) {
+            const int buf = u & 1, grp = u % S::NG, sbi = u / S::NG;
+            const TcUnit cur = nxt;
+            locate(u + 1, nxt);
+            const bool w = u < 2 || mbar_wait(empty + buf, ((u >> 1) - 1) & 1, abort_flag);
+            if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
+            // the delta of this site block (first stage of the block; its B buffer was
+            // last read by MMAs that completed before the empty wait above)
+            if (grp == 0 && tid < WG_S * COUT) {
+                const int a = tid / WG_S;
+                const long x = (sb0 + sbi) * WG_S + j;
+                uint8_t* bimg = Bsm + (sbi & 1) * S::B_IMG + a * WG_SBO;
+                uint32_t wd[12];
+                if (x < g.V) {
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        const uint4 v = __ldg(delta + ((long)a * 3 + q) * g.V + x);
+                        wd[4 * q] = v.x; wd[4 * q + 1] = v.y; wd[4 * q + 2] = v.z; wd[4 * q + 3] = v.w;
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 12; ++q) wd[q] = 0u;
+                }
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    *reinterpret_cast<uint4*>(bimg + ((WG_S * c + j) >> 3) * 128 + (j & 7) * 16) =
+                        make_uint4(wd[c], wd[3 + c], wd[6 + c], wd[9 + c]);
+            }
+            cp_async_wait_all();
+            uint8_t* img = Asm + buf * S::A_IMG + unit * WG_SBO;
+            if (cur.flags & 1) {
+                uint4 a[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) a[q] = rawp[q * WG_PT];
+                float2 mr[9], mi[9];
+                const bool copy = (cur.flags & 2) != 0;
+                if (!copy) {
+                    cpx<float> lk[9];
+                    tc_link(cur, lk);
+                    if (cur.flags & 4) tc_link_pairs<true>(lk, mr, mi);
+                    else tc_link_pairs<false>(lk, mr, mi);
+                }
+                wg_transport_unit(a, mr, mi, cur.ph, copy, img, j);
+            } else {
+                // no site or no path: zero rows (an earlier stage may have left values)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    *reinterpret_cast<uint4*>(img + ((WG_S * c + j) >> 3) * 128 + (j & 7) * 16) =
+                        make_uint4(0u, 0u, 0u, 0u);
+            }
+            if (nxt.flags & 1) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) cp_async16(raw_base + q * WG_PT * 16, in + ((long)b * 3 + q) * g.V + nxt.y);
+            }
+            cp_async_commit();
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_arrive(full + buf);
+        }
+    }
+
+    // read back: this warp's lane quarter (rows m = 32 quarter + lane), its quarter
+    // of the columns of every group; partial[block][p][n][m'] with m' = row of path p
+    if (ok && nst > 0) {
+        const bool w = mbar_wait(acc_full, 0, abort_flag);
+        if (__all_sync(0xffffffffu, w)) {
+            tc_fence_after();
+            const int quarter = warp & 3, wq = warp >> 2;      // the MMA warp (wq = 4) reads nothing
+            const int m = 32 * quarter + lane, ps = m / (8 * CIN), mr8 = m % (8 * CIN);
+            constexpr int CW = S::NN / 4 < 8 ? 8 : S::NN / 4;  // columns per warp (x8 loads)
+            for (int grp = 0; grp < S::NG; ++grp) {
+                const int p = grp * S::PPM + ps;
+                for (int c0 = wq * CW; c0 < (wq + 1) * CW && c0 < S::NN && wq < 4; c0 += 8) {
+                    uint32_t v0[8];
+                    tmem_ld8(tmem + ((uint32_t)(32 * quarter) << 16) + grp * S::NN + c0, v0);
+                    tmem_wait_ld1(v0);
+                    if (p < 9) {
+#pragma unroll
+                        for (int e = 0; e < 8; ++e) {
+                            const int n = c0 + e;
+                            if (n < 8 * COUT)
+                                partial[(((long)blockIdx.x * 9 + p) * 64 + n) * 64 + mr8] = __uint_as_float(v0[e]);
+                        }
+                    }
+                }
+            }
+        } else {
+            ok = false;
+        }
+    }
+
+    // drain: copies and MMAs complete (bounded) before TMEM is released
+    cp_async_wait_all();
+    tc_fence_before();
+    __syncthreads();
+    if (tid == WG_PT) {
+        tc_commit(drain);
+        if (!mbar_wait(drain, 0, nullptr)) ok = false;
+    }
+    if (!ok) atomicExch(err, 1);
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS)
+                     : "memory");
+    }
 }
 
 // G[p][a][b][s][t] (complex) += scale * combination of the summed partials
-__global__ void ptc_wgrad_reduce(const float* __restrict__ partial, int nchunk, int cin, int cout,
-                                 float2* grad, float scale) {
+// Q_p[n][m] (n = 8 a + 2 s + ri of the delta, m = 8 b + 2 t + ri' of T_p in):
+//   Re G = Q[re][re] + Q[im][im],  Im G = Q[im][re] - Q[re][im]   (delta conj(v))
+__global__ void ptc_wgrad_reduce(const float* __restrict__ partial, int nblk, int cin, int cout, float2* grad,
+                                 float scale) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int n = 9 * cout * cin * 16;
     if (e >= n) return;
@@ -776,14 +902,14 @@ __global__ void ptc_wgrad_reduce(const float* __restrict__ partial, int nchunk, 
     const int b = r % cin; r /= cin;
     const int a = r % cout;
     const int p = r / cout;
-    const int mre = 4 * a + s, mim = 32 + 4 * a + s, kre = 4 * b + t, kim = 32 + 4 * b + t;
+    const int nre = 8 * a + 2 * s, mre = 8 * b + 2 * t;
     double rr = 0, ii = 0, ir = 0, ri = 0;
-    for (int c = 0; c < nchunk; ++c) {
-        const float* q = partial + ((size_t)p * nchunk + c) * 4096;
-        rr += q[mre * 64 + kre];
-        ii += q[mim * 64 + kim];
-        ir += q[mim * 64 + kre];
-        ri += q[mre * 64 + kim];
+    for (int c = 0; c < nblk; ++c) {
+        const float* q = partial + ((size_t)c * 9 + p) * 4096;
+        rr += q[nre * 64 + mre];
+        ii += q[(nre + 1) * 64 + mre + 1];
+        ir += q[(nre + 1) * 64 + mre];
+        ri += q[nre * 64 + mre + 1];
     }
     grad[e].x += scale * (float)(rr + ii);
     grad[e].y += scale * (float)(ir - ri);
@@ -1019,32 +1145,48 @@ cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in
 }
 
 template <int CIN, int COUT>
-static cudaError_t wgrad_t(const PtcGeom& g, const void* in, const void* delta, float* partial, int nchunk,
+static cudaError_t wgrad_t(const PtcGeom& g, const void* in, const void* delta, float* partial, int nblk, int* err,
                            cudaStream_t st) {
-    const long ntiles = (g.V + PTC_TILE - 1) / PTC_TILE;
-    ptc_wgrad_kernel<CIN, COUT><<<9 * nchunk, PTC_BS, 0, st>>>(g, reinterpret_cast<const uint4*>(in),
-                                                               reinterpret_cast<const uint4*>(delta), partial, ntiles,
-                                                               nchunk);
+    using S = WgShape<CIN, COUT>;
+    // a block that allocates all 512 TMEM columns must be alone on its SM: ask for
+    // more shared memory than two blocks could share
+    constexpr int SMEM = S::TMEM_COLS == 512 && S::SMEM < 120 * 1024 ? 120 * 1024 : S::SMEM;
+    static_assert(SMEM <= 227 * 1024, "weight-gradient shared memory");
+    if (g.V >= (1L << 31)) return cudaErrorInvalidValue;
+    static int cfg_dev = -1;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (cfg_dev != dev) {
+        e = cudaFuncSetAttribute(ptc_wgrad_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        cfg_dev = dev;
+    }
+    const long nsb = (g.V + WG_S - 1) / WG_S;
+    ptc_wgrad_tc<CIN, COUT><<<nblk, WG_BS, SMEM, st>>>(g, reinterpret_cast<const uint4*>(in),
+                                                       reinterpret_cast<const uint4*>(delta), partial, nsb, err);
     return cudaGetLastError();
 }
 
 cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
-                             int nchunk, float2* grad, float scale, cudaStream_t st) {
+                             int nsm, float2* grad, float scale, int* err, cudaStream_t st) {
+    const long nsb = (g.V + WG_S - 1) / WG_S;
+    const int nblk = (int)std::min<long>(nsm, nsb);
     cudaError_t e;
-    if (cin == 1 && cout == 8) e = wgrad_t<1, 8>(g, in, delta, partial, nchunk, st);
-    else if (cin == 8 && cout == 8) e = wgrad_t<8, 8>(g, in, delta, partial, nchunk, st);
-    else if (cin == 8 && cout == 1) e = wgrad_t<8, 1>(g, in, delta, partial, nchunk, st);
-    else if (cin == 1 && cout == 1) e = wgrad_t<1, 1>(g, in, delta, partial, nchunk, st);
-    else if (cin == 1 && cout == 2) e = wgrad_t<1, 2>(g, in, delta, partial, nchunk, st);
-    else if (cin == 2 && cout == 2) e = wgrad_t<2, 2>(g, in, delta, partial, nchunk, st);
-    else if (cin == 2 && cout == 1) e = wgrad_t<2, 1>(g, in, delta, partial, nchunk, st);
-    else if (cin == 4 && cout == 4) e = wgrad_t<4, 4>(g, in, delta, partial, nchunk, st);
-    else if (cin == 1 && cout == 4) e = wgrad_t<1, 4>(g, in, delta, partial, nchunk, st);
-    else if (cin == 4 && cout == 1) e = wgrad_t<4, 1>(g, in, delta, partial, nchunk, st);
+    if (cin == 1 && cout == 8) e = wgrad_t<1, 8>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 8 && cout == 8) e = wgrad_t<8, 8>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 8 && cout == 1) e = wgrad_t<8, 1>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 1 && cout == 1) e = wgrad_t<1, 1>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 1 && cout == 2) e = wgrad_t<1, 2>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 2 && cout == 2) e = wgrad_t<2, 2>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 2 && cout == 1) e = wgrad_t<2, 1>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 4 && cout == 4) e = wgrad_t<4, 4>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 1 && cout == 4) e = wgrad_t<1, 4>(g, in, delta, partial, nblk, err, st);
+    else if (cin == 4 && cout == 1) e = wgrad_t<4, 1>(g, in, delta, partial, nblk, err, st);
     else return cudaErrorInvalidValue;
     if (e != cudaSuccess) return e;
     const int n = 9 * cout * cin * 16;
-    ptc_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(partial, nchunk, cin, cout, grad, scale);
+    ptc_wgrad_reduce<<<(n + 255) / 256, 256, 0, st>>>(partial, nblk, cin, cout, grad, scale);
     return cudaGetLastError();
 }
 

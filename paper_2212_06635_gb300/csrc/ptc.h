@@ -5,9 +5,6 @@
 
 namespace tmk {
 
-constexpr int PTC_TILE = 32;               // sites per tile of the weight-gradient kernel
-constexpr int PTC_BS = 128;                // threads per block (4 warps)
-constexpr int PTC_N = 3 * PTC_TILE;        // GEMM columns per tile (site, colour)
 constexpr int PTC_MAXC = 8;                // channels per layer
 
 struct PtcGeom {
@@ -21,8 +18,10 @@ struct PtcGeom {
 // out of its bound (the layer's output is then incomplete)
 cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* wemb,
                              int nsm, int* err, cudaStream_t st);
+// weight gradient of one layer into grad (scaled, accumulated); partial holds
+// 9 * 4096 floats per block, min(nsm, sites / 32) blocks
 cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
-                             int nchunk, float2* grad, float scale, cudaStream_t st);
+                             int nsm, float2* grad, float scale, int* err, cudaStream_t st);
 cudaError_t launch_ptc_embed_weights(const float2* W, int cin, int cout, void* fwd, void* adj, cudaStream_t st);
 cudaError_t launch_ptc_adam(float2* W, float2* m, float2* v, float2* grad, int n, float lr, float b1, float b2,
                             float eps, int step, cudaStream_t st);
