@@ -226,6 +226,12 @@ tm_status tm_ptc_init(tm_ptc* net, double scale, double noise, unsigned long lon
 tm_status tm_ptc_get_weights(const tm_ptc* net, double* weights);
 /* out = N(in): native FP32 light odd fields of ctx's lattice (device), stream-ordered. */
 tm_status tm_ptc_apply(tm_ptc* net, tm_ctx* ctx, void* out, const void* in, void* stream);
+/* Check of the bounded waits used by the PTC kernels (the paper has no
+ * counterpart): one GPU thread waits on an mbarrier that nothing arrives on,
+ * bounded by `seconds` (0 < seconds <= 10).  *timed_out = 1 when the bound ran
+ * out as designed (0: the phase completed, 2: the wait ended otherwise); the
+ * context stays usable.  Synchronous. */
+tm_status tm_wait_selftest(int device, double seconds, int* timed_out);
 /* Wait for the network's work queued on stream and report a layer kernel whose
  * bounded wait on the tensor cores ran out (TM_ERR_TIMEOUT; its output is then
  * incomplete).  tm_ptc_grad, tm_ptc_train and tm_solve_fcg check the same flag

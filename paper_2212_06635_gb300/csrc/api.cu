@@ -1645,6 +1645,21 @@ extern "C" tm_status tm_ptc_sync(tm_ptc* n, void* stream) {
     return ptc_check_flag(n);
 }
 
+extern "C" tm_status tm_wait_selftest(int device, double seconds, int* timed_out) {
+    if (!timed_out || !(seconds > 0) || seconds > 10) return fail(TM_ERR_ARG, "tm_wait_selftest: bad argument");
+    CK(cudaSetDevice(device));
+    int* d = nullptr;
+    CK(cudaMalloc(&d, sizeof(int)));
+    tm_status s = TM_OK;
+    int h = -1;
+    if (launch_ptc_wait_selftest((long long)(seconds * 1e9), d, nullptr) != cudaSuccess ||
+        cudaMemcpy(&h, d, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+        s = fail(TM_ERR_CUDA, "tm_wait_selftest: %s", cudaGetErrorString(cudaGetLastError()));
+    cudaFree(d);
+    *timed_out = h;
+    return s;
+}
+
 extern "C" tm_status tm_ptc_apply(tm_ptc* n, tm_ctx* c, void* out, const void* in, void* stream) {
     if (!n || !c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_ptc_apply: bad argument");
     CK(cudaSetDevice(c->device));

@@ -157,20 +157,39 @@ __device__ __forceinline__ bool mbar_test_sleep(uint64_t* b, uint32_t parity) {
 }
 
 // Wait for the completion of the phase with this parity.  Returns false, with
-// the block's abort flag set, after TC_WAIT_NS or as soon as another thread has
+// the block's abort flag set, after bound_ns or as soon as another thread has
 // set the flag, so one wait that runs out ends every role of the block.  With
 // abort_flag null only the time bound applies.
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                                          long long bound_ns = TC_WAIT_NS) {
     if (mbar_test(b, parity)) return true;
     const long long t0 = global_ns();
     while (!mbar_test_sleep(b, parity)) {
         if (abort_flag != nullptr && *abort_flag) return false;
-        if (global_ns() - t0 > TC_WAIT_NS) {
+        if (global_ns() - t0 > bound_ns) {
             if (abort_flag != nullptr) *abort_flag = 1;
             return false;
         }
     }
     return true;
+}
+
+// Check of the bounded wait: one thread waits on an mbarrier that no thread
+// arrives on.  *out = 1: the bound ran out and set the abort flag (expected);
+// 0: the phase completed; 2: the wait ended without the flag.
+__global__ void ptc_wait_selftest(long long bound_ns, int* out) {
+    __shared__ uint64_t b;
+    __shared__ int abort_flag;
+    if (threadIdx.x == 0) {
+        mbar_init(&b, 1);
+        abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const bool done = mbar_wait(&b, 0, &abort_flag, bound_ns);
+        *out = done ? 0 : (abort_flag ? 1 : 2);
+    }
 }
 
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -1229,6 +1248,11 @@ cudaError_t launch_ptc_loss_delta(const void* aL, const void* e, void* delta, co
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     sum_partials<<<1, 256, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ptc_wait_selftest(long long bound_ns, int* out, cudaStream_t st) {
+    ptc_wait_selftest<<<1, 32, 0, st>>>(bound_ns, out);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,8 @@ cudaError_t launch_ptc_extract_odd(int prec, const void* a, void* z, const PtcGe
 // loss sum ||z - e||^2 -> *out, delta = (z - e) / *ee on odd sites (0 elsewhere)
 cudaError_t launch_ptc_loss_delta(const void* aL, const void* e, void* delta, const PtcGeom& g, const double* ee,
                                   double* partial, double* out, cudaStream_t st);
+// one thread waits (bounded by bound_ns) on an mbarrier nobody arrives on; *out = 1 if the bound ran out
+cudaError_t launch_ptc_wait_selftest(long long bound_ns, int* out, cudaStream_t st);
 cudaError_t launch_ptc_gauss_odd(void* e, long vh, unsigned long long seed, unsigned long long stream,
                                  cudaStream_t st);
 

@@ -92,6 +92,7 @@ _sigs = {
     "tm_ptc_get_weights": [_vp, _vp],
     "tm_ptc_apply": [_vp, _vp, _vp, _vp, _vp],
     "tm_ptc_sync": [_vp, _vp],
+    "tm_wait_selftest": [ct.c_int, ct.c_double, ct.POINTER(ct.c_int)],
     "tm_ptc_grad": [_vp, _vp, _vp, _vp, ct.POINTER(ct.c_double), _vp, _vp],
     "tm_ptc_train": [_vp, ct.POINTER(_vp), ct.c_int, ct.c_int, ct.c_int, ct.c_int, ct.c_double, ct.c_ulonglong,
                      _vp, _vp],
@@ -307,6 +308,13 @@ def tm_ptc_get_weights(net):
 
 def tm_ptc_apply(net, ctx, out, inp, stream=None):
     _check(lib.tm_ptc_apply(net, ctx, ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_wait_selftest(seconds=1e-3, device=0):
+    """Bounded-wait check: returns 1 when a wait on an mbarrier nobody arrives on ran out."""
+    out = ct.c_int(-1)
+    _check(lib.tm_wait_selftest(device, seconds, ct.byref(out)))
+    return out.value
 
 
 def tm_ptc_sync(net, stream=None):

@@ -193,3 +193,16 @@ def test_training_reduces_loss_and_helps_fcg():
         tm.tm_ptc_destroy(net)
         for l in lats:
             l.close()
+
+
+def test_bounded_wait_runs_out_and_leaves_the_context_usable():
+    """The PTC kernels bound every mbarrier wait; a wait that nothing completes
+    must end after its bound with the abort flag set, and later work must run."""
+    import time
+    import torch
+    from paper_2212_06635_gb300 import tm
+    t0 = time.perf_counter()
+    assert tm.tm_wait_selftest(2e-3) == 1
+    assert time.perf_counter() - t0 < 5.0
+    x = torch.arange(1024, dtype=torch.float64, device="cuda")
+    assert float((x * 2).sum()) == 1023 * 1024
