@@ -22,6 +22,32 @@ PRECS = {"f64": 0, "f32": 1, "bf16": 2, "f16": 3}
 ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
 
 
+def ptc_grad_probe(dims, reps):
+    """Time tm_ptc_grad (forward, loss, 4 weight-gradient and 3 input-gradient
+    layers plus the host copies of the gradient) on a seeded pair."""
+    import time
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    u = F.gauge_field(dims, 1001)
+    r = F.odd_spinor(dims, 2001)
+    e = F.odd_spinor(dims, 2002)
+    ctx = tm.tm_create(dims, 0)
+    net = tm.tm_ptc_create([1, 8, 8, 8, 1])
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, 0.14, 1.69, mu=0.0015)
+        tm.tm_ptc_init(net, 0.5, 0.02, 1)
+        tm.tm_ptc_grad(net, ctx, r, e)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            tm.tm_ptc_grad(net, ctx, r, e)
+        ms = (time.perf_counter() - t0) * 1e3 / max(reps, 1)
+        print(f"dims {dims} PTC 1-8-8-8-1 loss + gradient: {ms:.3f} ms per pair (host inputs)")
+    finally:
+        tm.tm_ptc_destroy(net)
+        tm.tm_destroy(ctx)
+
+
 def ptc_probe(dims, reps):
     import torch
     from paper_2212_06635_gb300 import tm
@@ -65,6 +91,8 @@ def main():
     ap.add_argument("--ptc", action="store_true",
                     help="instead: apply a 1-8-8-8-1 PTC network (1 + reps) times; each application "
                          "launches its 4 layer kernels in order")
+    ap.add_argument("--ptc-grad", action="store_true",
+                    help="instead: loss and gradient of a 1-8-8-8-1 PTC network on one pair, (1 + reps) times")
     a = ap.parse_args()
     import torch
     from paper_2212_06635_gb300 import tm
@@ -72,6 +100,8 @@ def main():
     dims = tuple(a.dims)
     if a.ptc:
         return ptc_probe(dims, a.reps)
+    if a.ptc_grad:
+        return ptc_grad_probe(dims, a.reps)
     prec = PRECS[a.prec]
     nf = 2 if a.heavy else 1
     u = F.gauge_field(dims, 1001)
