@@ -374,12 +374,16 @@ def run_multishift(tm, args):
         shifts = [lam_t * 10.0 ** (-5 + 5 * k / 11) for k in range(CFG.N_SHIFTS)]
         out["lambda_max"] = lam
         bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
-        for name, sl in (("single_refined", tm.TM_F32), ("half_refined", tm.TM_F16), ("double", tm.TM_F64)):
+        # (multishift storage, refinement storage): Sec. 4.2's forms "single / double-single",
+        # "single / double-half", "half / double-half" and "double"
+        forms = (("single_refined", tm.TM_F32, tm.TM_F64), ("single_half_refined", tm.TM_F32, tm.TM_F16),
+                 ("half_refined", tm.TM_F16, tm.TM_F64), ("double", tm.TM_F64, tm.TM_F64))
+        for name, sl, rf in forms:
             xs = [torch.zeros_like(bd) for _ in shifts]
             _sync()
             t0 = time.perf_counter()
-            infos = tm.tm_solve_multishift(ctx, tm.TM_QH_SQ, shifts, xs, bd, tm.solve_params(tol=w.tol, sloppy=sl),
-                                           check=False)
+            infos = tm.tm_solve_multishift(ctx, tm.TM_QH_SQ, shifts, xs, bd,
+                                           tm.solve_params(tol=w.tol, sloppy=sl, refine=rf), check=False)
             _sync()
             out[name] = {"seconds": round(time.perf_counter() - t0, 4),
                          "max_true_rel_res": max(i.true_rel_res for i in infos),

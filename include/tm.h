@@ -94,6 +94,11 @@ typedef struct {
     double delta;        /* reliable-update trigger: ||r_sloppy|| < delta * ||r_true_last|| */
     int chunk;           /* iterations enqueued between two host checks (0 = default 16) */
     int use_graph;       /* capture the chunk in a CUDA graph and replay it */
+    tm_prec refine;      /* tm_solve_multishift only: storage precision of the
+                            shift-by-shift refinement CG; TM_F64 (0) = same as
+                            sloppy.  TM_F16 after an FP32 multishift is Sec. 4.2's
+                            "single precision MS-CG with double-half shift-by-shift
+                            refinement" */
 } tm_solve_params;
 
 typedef struct {

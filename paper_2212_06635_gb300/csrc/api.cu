@@ -1062,12 +1062,14 @@ extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const doub
         if (!(shifts[k] >= 0.0) || !x[k]) return fail(TM_ERR_ARG, "tm_solve_multishift: shifts must be >= 0");
     if (op != TM_MDAGM && op != TM_QH_SQ && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_solve_multishift: bad op");
     CKS(check_prec(sp->sloppy));
+    CKS(check_prec(sp->refine));
     CK(cudaSetDevice(c->device));
     CKS(check_solver_op(c, op));
     const cudaStream_t st = c->sstream;
     CKS(enter_solver(c, stream));
     CKS(ensure_prec(c, P64, st));
     CKS(ensure_prec(c, sp->sloppy, st));
+    if (sp->refine != TM_F64) CKS(ensure_prec(c, sp->refine, st));
     const int nf = nflav(op);
     const size_t b64sz = spinor_bytes(P64, 12 * nf, c->vh);
     std::vector<int> order(ns);
@@ -1084,13 +1086,16 @@ extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const doub
     tm_status s = nf == 1 ? multishift_dispatch<1>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st)
                           : multishift_dispatch<2>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st);
     tm_status worst = s;
-    // shift-by-shift refinement with mixed-precision CG (Sec. 4.2)
+    // shift-by-shift refinement with mixed-precision CG (Sec. 4.2), in its own
+    // storage precision when sp->refine names one
+    tm_solve_params rsp = *sp;
+    if (sp->refine != TM_F64) rsp.sloppy = sp->refine;
     for (int k = 0; k < ns; ++k) {
         tm_solve_info& inf = infos[order[k]];
         std::memset(&inf, 0, sizeof(inf));
         if (s != TM_OK) { inf.status = s; continue; }
-        tm_status r = nf == 1 ? solve_dispatch<1>(c, op, sh[k], sp, xk64[k], b64, &inf, st)
-                              : solve_dispatch<2>(c, op, sh[k], sp, xk64[k], b64, &inf, st);
+        tm_status r = nf == 1 ? solve_dispatch<1>(c, op, sh[k], &rsp, xk64[k], b64, &inf, st)
+                              : solve_dispatch<2>(c, op, sh[k], &rsp, xk64[k], b64, &inf, st);
         inf.iters += ms_iters;
         if (r != TM_OK && worst == TM_OK) worst = r;
         CKS(stage_out(c, nf, x[order[k]], WS_STAGE_X, xk64[k], st));

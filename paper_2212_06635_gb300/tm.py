@@ -35,7 +35,7 @@ class tm_params(ct.Structure):
 
 class tm_solve_params(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("maxiter", ct.c_int), ("sloppy", ct.c_int),
-                ("delta", ct.c_double), ("chunk", ct.c_int), ("use_graph", ct.c_int)]
+                ("delta", ct.c_double), ("chunk", ct.c_int), ("use_graph", ct.c_int), ("refine", ct.c_int)]
 
 
 class tm_solve_info(ct.Structure):
@@ -208,8 +208,9 @@ def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
     _check(lib.tm_apply_Mhat(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
 
 
-def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.1, chunk=16, use_graph=1):
-    return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph)
+def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.1, chunk=16, use_graph=1, refine=TM_F64):
+    """refine: multishift refinement storage precision (TM_F64 = same as sloppy)."""
+    return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph, refine)
 
 
 def tm_solve_cg(ctx, op, sp, x, b, stream=None, check=True):

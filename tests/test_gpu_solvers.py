@@ -86,8 +86,11 @@ def test_heavy_cg():
         lat.close()
 
 
-@pytest.mark.parametrize("sloppy", [0, 1, 3], ids=["f64", "f32", "f16"])
-def test_multishift_heavy_refined(sloppy):
+# (multishift storage, refinement storage); refine 0 = same as the multishift.
+# (1, 3) is Sec. 4.2's single-precision MS-CG with double-half refinement.
+@pytest.mark.parametrize("sloppy,refine", [(0, 0), (1, 0), (3, 0), (1, 3), (1, 2)],
+                         ids=["f64", "f32", "f16", "f32-f16", "f32-bf16"])
+def test_multishift_heavy_refined(sloppy, refine):
     dims = (4, 4, 4, 4)
     op, lat = _lat(dims, 1400, kappa=0.14, mu=0.0, mubar=0.1246, epsbar=0.135)
     tm = lat.tm
@@ -95,7 +98,7 @@ def test_multishift_heavy_refined(sloppy):
         b = F.odd_spinor(dims, 2400, 2)
         shifts = [0.3, 1e-4, 0.02, 1e-3]          # unsorted on purpose
         xs = [to_dev(np.zeros_like(b)) for _ in shifts]
-        sp = tm.solve_params(tol=1e-10, sloppy=sloppy)
+        sp = tm.solve_params(tol=1e-10, sloppy=sloppy, refine=refine)
         infos = tm.tm_solve_multishift(lat.ctx, tm.TM_QH_SQ, shifts, xs, to_dev(b), sp)
         for s, x, inf in zip(shifts, xs, infos):
             A = lambda v, s=s: op.heavy_sq(v) + s * v
