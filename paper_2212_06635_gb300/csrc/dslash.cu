@@ -33,18 +33,20 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
     }
     const long nf = cb_index(g, xf, yf, zf, tf);
     const long nb = cb_index(g, xb, yb, zb, tb);
+    constexpr bool SC = (P == PF16 || P == PB16);   // 16-bit: the scale joins the phase
     cpx<R> u[9];
     cpx<R> psi[NF * 12];
+    float sc;
     // forward
-    load_spinor<P, NF * 12>(pr.in, g.vh, nf, psi);
+    load_spinor_unscaled<P, NF * 12>(pr.in, g.vh, nf, psi, sc);
     load_link<P>(pr.gauge[po], g.vh, MU, i, u);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false>(acc[f], psi + 12 * f, u, ph_f);
+    for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false, SC>(acc[f], psi + 12 * f, u, SC ? ph_f * (R)sc : ph_f);
     // backward
-    load_spinor<P, NF * 12>(pr.in, g.vh, nb, psi);
+    load_spinor_unscaled<P, NF * 12>(pr.in, g.vh, nb, psi, sc);
     load_link<P>(pr.gauge[1 - po], g.vh, MU, nb, u);
 #pragma unroll
-    for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true>(acc[f], psi + 12 * f, u, ph_b);
+    for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true, SC>(acc[f], psi + 12 * f, u, SC ? ph_b * (R)sc : ph_b);
 }
 
 // Resident blocks the compiler must fit per SM.  Both light 16-bit passes fit in

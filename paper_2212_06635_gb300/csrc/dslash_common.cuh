@@ -15,9 +15,12 @@ namespace tmk {
 //   (1 + S g) psi = (h, S G^+ h),  h = psi_up + S G psi_down,
 // so only the two-spin half spinor h is transported by the link.
 // ---------------------------------------------------------------------------
-template <typename R, int MU, int S, bool DAG>
+// `factor` multiplies the half spinor: the boundary phase of a time hop, times
+// the neighbour's scale for 16-bit spinors (SCALED), which are passed unscaled;
+// scaling the 6 projected components costs half of scaling the 12 loaded ones.
+template <typename R, int MU, int S, bool DAG, bool SCALED = false>
 __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[4][3], const cpx<R>* psi,
-                                        const cpx<R> (&u)[9], R phase) {
+                                        const cpx<R> (&u)[9], R factor) {
     const R s = (R)S;
     cpx<R> h0[3], h1[3];
 #pragma unroll
@@ -36,7 +39,7 @@ __device__ __forceinline__ void hop_dir(cpx<R> (&acc)[4][3], const cpx<R>* psi,
             h0[c] = p0 - s * p2;
             h1[c] = p1 - s * p3;
         }
-        if (MU == 3) { h0[c] = phase * h0[c]; h1[c] = phase * h1[c]; }
+        if (MU == 3 || SCALED) { h0[c] = factor * h0[c]; h1[c] = factor * h1[c]; }
     }
     cpx<R> g0[3], g1[3];
 #pragma unroll

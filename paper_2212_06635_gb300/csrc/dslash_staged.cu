@@ -82,11 +82,8 @@ __device__ __forceinline__ void sp_from_smem(const uint4* s16, int unit0, const 
             }
         }
     }
-    if constexpr (P == PB16 || P == PF16) {
-        const float sc = sN[nidx * BS + t];
-#pragma unroll
-        for (int k = 0; k < NC; ++k) { s[k].re *= sc; s[k].im *= sc; }
-    }
+    // 16-bit spinors stay unscaled here: hop_dir applies the scale (sN) to the
+    // projected half spinor
 }
 
 template <int P, int NR>
@@ -222,14 +219,19 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
             constexpr int MU = decltype(MUc)::value;
             cpx<R> u[9];
             cpx<R> psi[NC];
+            constexpr bool SC = (P == PF16 || P == PB16);
             sp_from_smem<P, NC>(s16, (buf * 2 + 0) * G::SP16, sN, buf * 2 + 0, BS, t, psi);
             link_from_smem<P>(sL, (buf * 2 + 0) * G::NL, BS, t, u);
+            R fac = MU == 3 ? phf : (R)1;
+            if constexpr (SC) fac *= (R)sN[(buf * 2 + 0) * BS + t];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false>(acc[f], psi + 12 * f, u, MU == 3 ? phf : (R)1);
+            for (int f = 0; f < NF; ++f) hop_dir<R, MU, -1, false, SC>(acc[f], psi + 12 * f, u, fac);
             sp_from_smem<P, NC>(s16, (buf * 2 + 1) * G::SP16, sN, buf * 2 + 1, BS, t, psi);
             link_from_smem<P>(sL, (buf * 2 + 1) * G::NL, BS, t, u);
+            fac = MU == 3 ? phb : (R)1;
+            if constexpr (SC) fac *= (R)sN[(buf * 2 + 1) * BS + t];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true>(acc[f], psi + 12 * f, u, MU == 3 ? phb : (R)1);
+            for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true, SC>(acc[f], psi + 12 * f, u, fac);
         };
         cp_wait<1>();
         consume(std::integral_constant<int, 0>{}, 0);
@@ -284,6 +286,11 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
         } else {
             cpx<R> psi[NC];
             sp_from_smem<P, NC>(s16, ue + G::CLV16, sN, 4, BS, t, psi);
+            if constexpr (P == PB16 || P == PF16) {
+                const R sc = (R)sN[4 * BS + t];
+#pragma unroll
+                for (int k = 0; k < NC; ++k) psi[k] = sc * psi[k];
+            }
             R m[72];
             reals_from_smem<P, 72>(s16, ue, BS, t, m);
             const R k2 = (R)(pr.kappa * pr.kappa);

@@ -175,6 +175,21 @@ __device__ __forceinline__ void load_spinor(const void* base, long vh, long i,
     }
 }
 
+// as load_spinor, but 16-bit spinors stay unscaled and their per-site scale is
+// returned in sc (1 for FP32 / FP64)
+template <int P, int NC>
+__device__ __forceinline__ void load_spinor_unscaled(const void* base, long vh, long i,
+                                                     cpx<typename PT<P>::R>* s, float& sc) {
+    using R = typename PT<P>::R;
+    load_reals<P, 2 * NC>(base, vh, i, 0, reinterpret_cast<R*>(s));
+    sc = 1.f;
+    if constexpr (P == PB16 || P == PF16) {
+        const float* nrm = reinterpret_cast<const float*>(
+            reinterpret_cast<const char*>(base) + (size_t)vh * NC * 2 * 2);
+        sc = __ldg(nrm + i);
+    }
+}
+
 template <int P, int NC>
 __device__ __forceinline__ void store_spinor(void* base, long vh, long i,
                                              const cpx<typename PT<P>::R>* s) {
