@@ -1416,6 +1416,7 @@ struct tm_ptc {
     void* tmp32[2] = {};
     int nsm = 0;
     int* derr = nullptr;       // set by a layer kernel whose tensor-core wait ran out of its bound
+    void* zmix = nullptr;      // per-path mixed fields of the layers with one output channel (9 channels)
 };
 
 static size_t ptc_nw(const tm_ptc* n, int l) { return (size_t)9 * n->ch[l + 1] * n->ch[l] * 16; }
@@ -1471,6 +1472,7 @@ static void ptc_free_acts(tm_ptc* n) {
     for (auto& a : n->act) { cudaFree(a); a = nullptr; }
     for (auto& d : n->del) { cudaFree(d); d = nullptr; }
     cudaFree(n->dpart); n->dpart = nullptr;
+    cudaFree(n->zmix); n->zmix = nullptr;
     cudaFree(n->e32); cudaFree(n->r32); cudaFree(n->tmp32[0]); cudaFree(n->tmp32[1]);
     n->e32 = n->r32 = n->tmp32[0] = n->tmp32[1] = nullptr;
     n->V = 0;
@@ -1500,6 +1502,7 @@ static tm_status ptc_buffers(tm_ptc* n, const tm_ctx* c) {
     for (int l = 0; l <= n->L; ++l) CK(cudaMalloc(&n->act[l], (size_t)n->ch[l] * 3 * 16 * V));
     for (auto& d : n->del) CK(cudaMalloc(&d, (size_t)PTC_MAXC * 3 * 16 * V));
     CK(cudaMalloc(&n->dpart, sizeof(double) * ((V + 255) / 256)));
+    CK(cudaMalloc(&n->zmix, (size_t)9 * 3 * 16 * V));
     const size_t s32 = spinor_bytes(P32, 12, c->vh);
     CK(cudaMalloc(&n->e32, s32));
     CK(cudaMalloc(&n->r32, s32));
@@ -1603,7 +1606,8 @@ static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaS
     const PtcGeom g = ptc_geom(c);
     CK(launch_ptc_embed_odd(P32, r, n->act[0], g, st));
     for (int l = 0; l < n->L; ++l)
-        CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, n->derr, st));
+        CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, n->derr, n->zmix,
+                            st));
     if (z) CK(launch_ptc_extract_odd(P32, n->act[n->L], z, g, st));
     return TM_OK;
 }
@@ -1618,7 +1622,7 @@ static tm_status ptc_backward(tm_ptc* n, tm_ctx* c, const void* e, float scale, 
                             n->derr, st));
         if (l > 0) {
             CK(launch_ptc_layer(n->ch[l + 1], n->ch[l], g, n->del[cur], n->del[1 - cur], n->wa[l], n->nsm, n->derr,
-                                st));
+                                n->zmix, st));
             cur = 1 - cur;
         }
     }

@@ -90,18 +90,22 @@ constexpr int TC_BS = TC_PT + 32;          // + the MMA warp = 16 warps
 constexpr int TC_STAGES = 2;               // transport stage buffers
 constexpr long long TC_WAIT_NS = 1000000000LL;   // bound on every mbarrier wait (1 s)
 
-template <int CIN, int COUT>
+// MIX: the mixing half of a layer with one output channel (see ptc_layer_mix):
+// only the identity path, N = 9 paths x 8 rows (padded to 80), 9 output channels.
+template <int CIN, int COUT, bool MIX = false>
 struct TcShape {
+    static constexpr int NPATH = MIX ? 1 : 9;                // paths transported
+    static constexpr int NOUT = MIX ? 9 : COUT;              // output channels written
     static constexpr int KCH = CIN < 2 ? 2 : CIN;            // K = 8 KCH >= 16 (one MMA K step)
-    static constexpr int NN = 8 * COUT < 16 ? 16 : 8 * COUT; // N per colour (multiple of 16 for M = 128)
+    static constexpr int NN = MIX ? 80 : (8 * COUT < 16 ? 16 : 8 * COUT);   // N per colour (multiple of 16)
     static constexpr int GPP = CIN < TC_G ? CIN : TC_G;      // site groups per path
     static constexpr int NPS = TC_G / GPP;                   // paths per stage (small CIN: one path per group)
     static constexpr int CPG = CIN / GPP;                    // input channels per thread
-    static constexpr int NSTG = (9 + NPS - 1) / NPS;         // stages per tile
+    static constexpr int NSTG = (NPATH + NPS - 1) / NPS;     // stages per tile
     static constexpr int A_COL = TC_M * 16 * KCH;            // bytes of one (path, colour) A image
     static constexpr int A_STAGE = NPS * 3 * A_COL;
     static constexpr int W_PATH = NN * 16 * KCH;             // bytes of one path's B image
-    static constexpr int W_ALL = 9 * W_PATH;
+    static constexpr int W_ALL = NPATH * W_PATH;
     static constexpr int TMEM_COLS = 3 * NN <= 32 ? 32 : (3 * NN <= 64 ? 64 : (3 * NN <= 128 ? 128 : 256));
     static constexpr int RAW = CPG * 3 * TC_PT * 16;         // cp.async slots: [channel][vector][thread]
     static constexpr int SMEM = W_ALL + TC_STAGES * A_STAGE + RAW + 128;   // + mbarriers, TMEM address, abort flag
@@ -380,7 +384,7 @@ __device__ __forceinline__ void tc_copy_channel(const uint4 (&a)[3], uint8_t* im
 // accumulators, read this warp's TMEM lane quarter (rows 32 quarter + lane =
 // sites of the tile) for its output channels, release the accumulators and
 // store the BF16 output vectors.  False if the wait ran out (warp-uniform).
-template <typename S, int COUT>
+template <typename S, int COUT>   // COUT = output channels written
 __device__ __forceinline__ bool tc_epilogue(uint32_t tmem, uint64_t* acc_full, uint64_t* acc_empty, uint32_t j,
                                             volatile int* abort_flag, int quarter, int wg, int lane, long tile,
                                             const PtcGeom& g, uint4* __restrict__ out) {
@@ -427,11 +431,11 @@ __device__ __forceinline__ bool tc_epilogue(uint32_t tmem, uint64_t* acc_full, u
     return true;
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool MIX>
 __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4* __restrict__ in,
                                                         uint4* __restrict__ out, const uint4* __restrict__ wimg,
                                                         long ntiles, int* err) {
-    using S = TcShape<CIN, COUT>;
+    using S = TcShape<CIN, COUT, MIX>;
     extern __shared__ __align__(1024) uint8_t smem[];
     uint8_t* Wsm = smem;                                   // 9 paths of B images
     uint8_t* Asm = smem + S::W_ALL;                        // TC_STAGES stage buffers of A images
@@ -496,7 +500,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
 #pragma unroll 1
                     for (int q = 0; q < S::NPS; ++q) {
                         const int pp = stg * S::NPS + q;
-                        if (pp >= 9) break;
+                        if (pp >= S::NPATH) break;
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -513,7 +517,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
             }
             ok = __shfl_sync(0xffffffffu, ok, 0);
             if (!ok) break;
-            if (!tc_epilogue<S, COUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
+            if (!tc_epilogue<S, S::NOUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
                 ok = false;
                 break;
             }
@@ -528,7 +532,8 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
         TcSite site = tc_site(g, (long)blockIdx.x * TC_SITES + r), nsite = site;
         TcUnit nxt;
-        tc_locate(g, site, pi, nxt);
+        nxt.flags = 0;
+        if (pi < S::NPATH) tc_locate(g, site, pi, nxt);
         if (nxt.flags & 1) {
 #pragma unroll
             for (int k = 0; k < S::CPG; ++k)
@@ -547,7 +552,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                     const int np = (last ? 0 : (stg + 1) * S::NPS) + pi;
                     if (last) nsite = tc_site(g, nt * TC_SITES + r);
                     nxt.flags = 0;
-                    if (nt < ntiles) tc_locate(g, nsite, np, nxt);
+                    if (nt < ntiles && np < S::NPATH) tc_locate(g, nsite, np, nxt);
                 }
                 // every lane of a warp runs the same iterations, so the vote keeps the
                 // warp together on the way out and at the epilogue's aligned loads
@@ -589,7 +594,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                 mbar_arrive(full + buf);
             }
             if (!ok) break;
-            if (!tc_epilogue<S, COUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
+            if (!tc_epilogue<S, S::NOUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
                 ok = false;
                 break;
             }
@@ -613,6 +618,67 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS)
                      : "memory");
     }
+}
+
+// ---------------------------------------------------------------------------
+// Layers with one output channel and C_in > 1 (8->1, 4->1, 2->1) mix first:
+// the spin-space weights commute with the colour-space transport, so
+//   out(x) = sum_p T_p (sum_b W_p^{0b} in^b)(x) = sum_p (T_p z_p)(x),
+// z_p = sum_b W_p^{0b} in^b at every site.  ptc_layer_tc<CIN, 1, true> computes
+// the nine z_p on the tensor cores (identity path, N = 9 x 8 rows); ptc_tsum then
+// transports one channel per path instead of C_in.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) ptc_tsum(PtcGeom g, const uint4* __restrict__ z, uint4* __restrict__ out) {
+    const long xl = (long)blockIdx.x * 256 + threadIdx.x;
+    if (xl >= g.V) return;
+    const TcSite site = tc_site(g, xl);
+    cpx<float> acc[12];   // complex (spin s, colour c) at 3 s + c
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const uint4 w = __ldg(z + (long)q * g.V + xl);
+        const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const float2 h = h2f2<PB16>(ws[e]);
+            acc[4 * q + e] = C(h.x, h.y);
+        }
+    }
+#pragma unroll 1
+    for (int p = 1; p < 9; ++p) {
+        TcUnit f;
+        tc_locate(g, site, p, f);
+        cpx<float> u[9];
+        tc_link(f, u);
+        const bool dag = (f.flags & 4) != 0;
+        cpx<float> v[12];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const uint4 w = __ldg(z + ((long)p * 3 + q) * g.V + f.y);
+            const uint32_t ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int e = 0; e < 4; ++e) {
+                const float2 h = h2f2<PB16>(ws[e]);
+                v[4 * q + e] = C(h.x, h.y);
+            }
+        }
+#pragma unroll
+        for (int sp = 0; sp < 4; ++sp)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cpx<float> t = C(0.f, 0.f);
+#pragma unroll
+                for (int d = 0; d < 3; ++d) {
+                    if (dag) cfma_cj(t, u[3 * d + c], v[3 * sp + d]);
+                    else cfma(t, u[3 * c + d], v[3 * sp + d]);
+                }
+                acc[3 * sp + c] = acc[3 * sp + c] + f.ph * t;
+            }
+    }
+#pragma unroll
+    for (int q = 0; q < 3; ++q)
+        out[(long)q * g.V + xl] = make_uint4(pack2(acc[4 * q].re, acc[4 * q].im), pack2(acc[4 * q + 1].re, acc[4 * q + 1].im),
+                                             pack2(acc[4 * q + 2].re, acc[4 * q + 2].im),
+                                             pack2(acc[4 * q + 3].re, acc[4 * q + 3].im));
 }
 
 // ---------------------------------------------------------------------------
@@ -949,21 +1015,25 @@ __device__ __forceinline__ int rev_path(int p) { return p == 0 ? 0 : (p <= 4 ? p
 // with W'_p[b][a][t][s] = conj(W_{rev p}[a][b][s][t]).
 __global__ void ptc_embed_weights(const float2* __restrict__ W, int cin, int cout, int adjoint, uint16_t* img) {
     const int cin_l = adjoint ? cout : cin, cout_l = adjoint ? cin : cout;
-    const int kch = cin_l < 2 ? 2 : cin_l, nn = 8 * cout_l < 16 ? 16 : 8 * cout_l;
+    // a layer with fewer output than input channels (one output channel) mixes
+    // first: one B image whose rows are n = 8 p + 2 s + ri over the 9 paths
+    const bool mix = cin_l > cout_l;
+    const int kch = cin_l < 2 ? 2 : cin_l, nn = mix ? 80 : (8 * cout_l < 16 ? 16 : 8 * cout_l);
     const int per_path = nn * 8 * kch;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= 9 * per_path) return;
-    const int p = e / per_path;
-    int rem = e - p * per_path;
+    if (e >= (mix ? 1 : 9) * per_path) return;
+    const int pb = e / per_path;
+    int rem = e - pb * per_path;
     const int kr = rem & 7; rem >>= 3;   // k % 8
     const int nr = rem & 7; rem >>= 3;   // n % 8
     const int kc = rem % kch;            // k / 8
     const int ng = rem / kch;            // n / 8
     const int n = 8 * ng + nr, k = 8 * kc + kr;
-    const int ao = n >> 3, so = (n >> 1) & 3, rim = n & 1;   // output channel, spin, re/im
+    const int p = mix ? (n >> 3) : pb;                       // path
+    const int ao = mix ? 0 : (n >> 3), so = (n >> 1) & 3, rim = n & 1;   // output channel, spin, re/im
     const int bi = k >> 3, si = (k >> 1) & 3, cim = k & 1;   // input channel, spin, re/im
     float v = 0.f;
-    if (ao < cout_l && bi < cin_l) {
+    if (p < 9 && ao < cout_l && bi < cin_l) {
         float2 w;
         if (!adjoint) {
             w = W[(((p * cout + ao) * cin + bi) * 4 + so) * 4 + si];
@@ -1125,10 +1195,10 @@ __global__ void ptc_gauss_odd(float4* e, long vh, unsigned long long seed, unsig
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-template <int CIN, int COUT>
+template <int CIN, int COUT, bool MIX = false>
 static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const void* w, int nsm, int* err,
                            cudaStream_t st) {
-    using S = TcShape<CIN, COUT>;
+    using S = TcShape<CIN, COUT, MIX>;
     static_assert(S::SMEM <= 227 * 1024, "layer shared memory");
     if (g.V >= (1L << 31)) return cudaErrorInvalidValue;   // site indices of the layer kernel are 32-bit
     static int cfg_dev = -1;
@@ -1136,30 +1206,40 @@ static cudaError_t layer_t(const PtcGeom& g, const void* in, void* out, const vo
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (cfg_dev != dev) {
-        e = cudaFuncSetAttribute(ptc_layer_tc<CIN, COUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
+        e = cudaFuncSetAttribute(ptc_layer_tc<CIN, COUT, MIX>, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM);
         if (e != cudaSuccess) return e;
         cfg_dev = dev;
     }
     const long ntiles = (g.V + TC_SITES - 1) / TC_SITES;
     const long grid = std::min<long>(ntiles, nsm);
-    ptc_layer_tc<CIN, COUT><<<(unsigned)grid, TC_BS, S::SMEM, st>>>(
+    ptc_layer_tc<CIN, COUT, MIX><<<(unsigned)grid, TC_BS, S::SMEM, st>>>(
         g, reinterpret_cast<const uint4*>(in), reinterpret_cast<uint4*>(out), reinterpret_cast<const uint4*>(w),
         ntiles, err);
     return cudaGetLastError();
 }
 
+template <int CIN>
+static cudaError_t mixed_first(const PtcGeom& g, const void* in, void* out, const void* w, int nsm, int* err,
+                               void* zbuf, cudaStream_t st) {
+    cudaError_t e = layer_t<CIN, 1, true>(g, in, zbuf, w, nsm, err, st);
+    if (e != cudaSuccess) return e;
+    ptc_tsum<<<(unsigned)((g.V + 255) / 256), 256, 0, st>>>(g, reinterpret_cast<const uint4*>(zbuf),
+                                                           reinterpret_cast<uint4*>(out));
+    return cudaGetLastError();
+}
+
 cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* w, int nsm,
-                             int* err, cudaStream_t st) {
+                             int* err, void* zbuf, cudaStream_t st) {
     if (cin == 1 && cout == 8) return layer_t<1, 8>(g, in, out, w, nsm, err, st);
     if (cin == 8 && cout == 8) return layer_t<8, 8>(g, in, out, w, nsm, err, st);
-    if (cin == 8 && cout == 1) return layer_t<8, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 8 && cout == 1) return mixed_first<8>(g, in, out, w, nsm, err, zbuf, st);
     if (cin == 1 && cout == 1) return layer_t<1, 1>(g, in, out, w, nsm, err, st);
     if (cin == 1 && cout == 2) return layer_t<1, 2>(g, in, out, w, nsm, err, st);
     if (cin == 2 && cout == 2) return layer_t<2, 2>(g, in, out, w, nsm, err, st);
-    if (cin == 2 && cout == 1) return layer_t<2, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 2 && cout == 1) return mixed_first<2>(g, in, out, w, nsm, err, zbuf, st);
     if (cin == 4 && cout == 4) return layer_t<4, 4>(g, in, out, w, nsm, err, st);
     if (cin == 1 && cout == 4) return layer_t<1, 4>(g, in, out, w, nsm, err, st);
-    if (cin == 4 && cout == 1) return layer_t<4, 1>(g, in, out, w, nsm, err, st);
+    if (cin == 4 && cout == 1) return mixed_first<4>(g, in, out, w, nsm, err, zbuf, st);
     return cudaErrorInvalidValue;
 }
 

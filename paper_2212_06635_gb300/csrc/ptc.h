@@ -15,9 +15,11 @@ struct PtcGeom {
 };
 
 // one layer on the tensor cores; *err is set to 1 if a wait on the tensor cores ran
-// out of its bound (the layer's output is then incomplete)
+// out of its bound (the layer's output is then incomplete).  Layers with one
+// output channel and cin > 1 mix first into zbuf (9 x 3 x 16 bytes per site)
+// and transport it afterwards; other layers ignore zbuf.
 cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in, void* out, const void* wemb,
-                             int nsm, int* err, cudaStream_t st);
+                             int nsm, int* err, void* zbuf, cudaStream_t st);
 // weight gradient of one layer into grad (scaled, accumulated); partial holds
 // 9 * 4096 floats per block, min(nsm, sites / 32) blocks
 cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
