@@ -851,12 +851,19 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
         const int ps = unit / CIN, b = unit % CIN;
         const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
         const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
+        // site coordinates change once per site block (every NG stages)
+        TcSite lsite;
+        long lsb = -1;
         auto locate = [&](int u, TcUnit& f) {
             f.flags = 0;
             if (u >= nst) return;
             const int grp = u % S::NG;
             const long sb = sb0 + u / S::NG;
-            tc_locate(g, tc_site(g, sb * WG_S + j), grp * S::PPM + ps, f);
+            if (sb != lsb) {
+                lsite = tc_site(g, sb * WG_S + j);
+                lsb = sb;
+            }
+            tc_locate(g, lsite, grp * S::PPM + ps, f);
         };
         TcUnit nxt;
         locate(0, nxt);
