@@ -107,11 +107,7 @@ struct TcShape {
     static constexpr int W_PATH = NN * 16 * KCH;             // bytes of one path's B image
     static constexpr int W_ALL = NPATH * W_PATH;
     static constexpr int TMEM_COLS = 3 * NN <= 32 ? 32 : (3 * NN <= 64 ? 64 : (3 * NN <= 128 ? 128 : 256));
-    // transport on the tensor cores for 4 and 8 input channels (not for the mixing half)
-    static constexpr bool TCT = !MIX && (CIN == 4 || CIN == 8);
-    static constexpr int RAW_WARP = 24 * CIN * 16;           // TCT: a warp's slot, 4 pairs x 2 sites x CIN x 3 vectors
-    static constexpr int RAW = TCT ? (TC_PT / 32) * RAW_WARP  // cp.async slots
-                                   : CPG * 3 * TC_PT * 16;   // per thread: [channel][vector][thread]
+    static constexpr int RAW = CPG * 3 * TC_PT * 16;         // cp.async slots: [channel][vector][thread]
     static constexpr int SMEM = W_ALL + TC_STAGES * A_STAGE + RAW + 128;   // + mbarriers, TMEM address, abort flag
     // kind::f16 instruction descriptor: D F32 (bits 4-5 = 1), A and B BF16 (bits 7-9, 10-12 = 1),
     // both K-major, N >> 3 at bit 17, M >> 4 at bit 24
@@ -297,27 +293,6 @@ __device__ __forceinline__ void tc_locate(const PtcGeom& g, const TcSite& s, int
 #pragma unroll
     for (int k = 0; k < 6; ++k) f.link[k] = __ldg(base + (long)(mu * 6 + k) * g.vh);
     f.flags = fwd ? 1 : 5;
-}
-
-// lexicographic neighbour of site x (coordinates c) along path p (1..8; 0 = x)
-__device__ __forceinline__ int tc_neighbor(const PtcGeom& g, const int (&c)[4], int x, int p) {
-    if (p == 0) return x;
-    const int mu = (p - 1) & 3;
-    const int L = mu == 0 ? g.X : (mu == 1 ? g.Y : (mu == 2 ? g.Z : g.T));
-    const int st = mu == 0 ? 1 : (mu == 1 ? g.X : (mu == 2 ? g.X * g.Y : g.X * g.Y * g.Z));
-    const int cm = c[mu];
-    if (p <= 4) return (cm + 1 == L) ? x - (L - 1) * st : x + st;
-    return (cm == 0) ? x + (L - 1) * st : x - st;
-}
-
-// D = A B, m16n8k16, BF16 in, FP32 out (standard register fragments)
-__device__ __forceinline__ void mma_bf16_16816(float (&d)[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
-                                               uint32_t b0, uint32_t b1) {
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
-        "{%10, %10, %10, %10};"
-        : "=f"(d[0]), "=f"(d[1]), "=f"(d[2]), "=f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1), "f"(0.f));
 }
 
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
@@ -547,126 +522,6 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                 break;
             }
         }
-    } else if constexpr (S::TCT) {
-        // ---- transport warps, transport on the tensor cores: warp w owns the 4 site
-        // pairs (rows 2 (4 w + i) + {0, 1} of the tile).  Per pair and path one
-        // m16n8k16 BF16 MMA per 2 input channels: A = the real embedding of the two
-        // sites' links (rows (site, colour, re | im), K = (site, colour, re/im)),
-        // B = the neighbours' activation words (K x 8 (channel, spin) columns),
-        // D = the transported components, stored as the stage's A image.
-        const int gq = lane >> 2, t4 = lane & 3;             // fragment group / thread in group
-        const int so = lane >> 4, cc = gq & 3;               // A and D rows of this lane: site of the pair, colour
-        uint8_t* rawb = Raw + warp * S::RAW_WARP;            // [pair 4][site 2][channel][vector 3] uint4
-        const uint32_t raw_base = smem_addr(rawb);
-        const uint32_t* raw32 = reinterpret_cast<const uint32_t*>(rawb);
-        constexpr int NCH = 24 * CIN;                        // 16-byte chunks per warp and stage
-        uint32_t u = 0, j = 0;
-        int pc[4][5];                                        // pairs of the tile: x0, then coordinates
-        auto pair_coords = [&](long tl) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                const long x0 = tl * TC_SITES + 2 * (4 * warp + i);
-                const TcSite s0 = tc_site(g, x0);
-                pc[i][0] = s0.valid ? s0.x : -1;
-                pc[i][1] = s0.c[0]; pc[i][2] = s0.c[1]; pc[i][3] = s0.c[2]; pc[i][4] = s0.c[3];
-            }
-        };
-        // activation words of path p for the warp's pairs -> the slot (cp.async)
-        auto issue = [&](int p) {
-#pragma unroll
-            for (int k = 0; k < NCH / 32; ++k) {
-                const int ci = lane + 32 * k;
-                const int q = ci % 3, b = (ci / 3) % CIN, o = (ci / (3 * CIN)) & 1, i = ci / (6 * CIN);
-                if (pc[i][0] >= 0) {
-                    const int c4[4] = {pc[i][1] + o, pc[i][2], pc[i][3], pc[i][4]};
-                    const int y = tc_neighbor(g, c4, pc[i][0] + o, p);
-                    cp_async16(raw_base + ci * 16, in + ((long)b * 3 + q) * g.V + y);
-                }
-            }
-            cp_async_commit();
-        };
-        // this lane's link word of path p for each pair: (Re, Im) of M[cc][t4] at the
-        // pair's site so, BF16 (identity for p = 0)
-        auto links = [&](int p, uint32_t (&lw)[4]) {
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                lw[i] = 0u;
-                if (cc < 3 && t4 < 3 && pc[i][0] >= 0) {
-                    if (p == 0) lw[i] = (cc == t4) ? 0x00003F80u : 0u;
-                    else lw[i] = __ldg(g.lp + ((long)(p - 1) * 9 + 3 * cc + t4) * g.V + pc[i][0] + so);
-                }
-            }
-        };
-        uint32_t lw[4], lwn[4];
-        pair_coords(blockIdx.x);
-        issue(0);
-        links(0, lw);
-        for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
-            int pcur[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) pcur[i] = pc[i][0];
-            for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
-                const int buf = u % TC_STAGES;
-                const bool w = u < TC_STAGES || mbar_wait(empty + buf, ((u / TC_STAGES) - 1) & 1, abort_flag);
-                if (!__all_sync(0xffffffffu, w)) {
-                    ok = false;
-                    break;
-                }
-                cp_async_wait_all();
-                __syncwarp();                                // every lane's copies have landed
-                uint32_t bw[4][CIN / 2][2];                  // B fragments of the stage
-#pragma unroll
-                for (int i = 0; i < 4; ++i)
-#pragma unroll
-                    for (int jj = 0; jj < CIN / 2; ++jj)
-#pragma unroll
-                        for (int o = 0; o < 2; ++o)
-                            bw[i][jj][o] = (t4 < 3) ? raw32[((i * 2 + o) * CIN + 2 * jj + (gq >> 2)) * 12 + 3 * (gq & 3) + t4]
-                                                   : 0u;
-                __syncwarp();                                // the slot is free for the next stage
-                {
-                    const bool last = stg + 1 == S::NSTG;
-                    const long nt = last ? tile + gridDim.x : tile;
-                    if (last) pair_coords(nt);
-                    if (nt < ntiles) {
-                        issue(last ? 0 : stg + 1);
-                        links(last ? 0 : stg + 1, lwn);
-                    } else {
-                        cp_async_commit();
-#pragma unroll
-                        for (int i = 0; i < 4; ++i) lwn[i] = 0u;
-                    }
-                }
-                uint8_t* img = Asm + (long)buf * S::A_STAGE;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    if (pcur[i] < 0) continue;               // warp-uniform
-                    const uint32_t re = lw[i] ^ 0x80000000u;                 // (Re, -Im)
-                    const uint32_t im = __byte_perm(lw[i], 0u, 0x1032);     // (Im, Re)
-                    const uint32_t a0 = so == 0 ? re : 0u, a1 = so == 0 ? im : 0u;
-                    const uint32_t a2 = so == 1 ? re : 0u, a3 = so == 1 ? im : 0u;
-                    const int row = 2 * (4 * warp + i) + so;
-                    uint8_t* dst = img + cc * S::A_COL + (row >> 3) * (128 * S::KCH) + (row & 7) * 16 + 8 * (t4 & 1);
-#pragma unroll
-                    for (int jj = 0; jj < CIN / 2; ++jj) {
-                        float d[4];
-                        mma_bf16_16816(d, a0, a1, a2, a3, bw[i][jj][0], bw[i][jj][1]);
-                        if (cc < 3)
-                            *reinterpret_cast<uint2*>(dst + (2 * jj + (t4 >> 1)) * 128) =
-                                make_uint2(pack2(d[0], d[2]), pack2(d[1], d[3]));
-                    }
-                }
-#pragma unroll
-                for (int i = 0; i < 4; ++i) lw[i] = lwn[i];
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                mbar_arrive(full + buf);
-            }
-            if (!ok) break;
-            if (!tc_epilogue<S, S::NOUT>(tmem, acc_full, acc_empty, j, abort_flag, quarter, wg, lane, tile, g, out)) {
-                ok = false;
-                break;
-            }
-        }
     } else {
         // ---- transport warps
         const int r = tid % TC_SITES, grp = tid / TC_SITES;   // site r of the tile, site group
@@ -762,32 +617,6 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         tc_fence_after();
         asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"((uint32_t)S::TMEM_COLS)
                      : "memory");
-    }
-}
-
-// Transport links of the eight hop paths as BF16 (re, im) pairs in lexicographic
-// site order: lp[(p - 1) * 9 + 3 c + d][x] = ph M[c][d], M = U_mu(x) for
-// p = 1..4 (mu = p - 1) and U_mu(x - mu)^dagger for p = 5..8, ph the time
-// boundary phase of the hop.  Operand A of the layer kernel's tensor-core
-// transport; rebuilt whenever the gauge field or the boundary phase changes.
-__global__ void __launch_bounds__(256) ptc_links(PtcGeom g, uint32_t* __restrict__ lp) {
-    const long xl = (long)blockIdx.x * 256 + threadIdx.x;
-    if (xl >= g.V) return;
-    const TcSite site = tc_site(g, xl);
-#pragma unroll 1
-    for (int p = 1; p < 9; ++p) {
-        TcUnit f;
-        tc_locate(g, site, p, f);
-        cpx<float> u[9];
-        tc_link(f, u);
-        const bool dag = (f.flags & 4) != 0;
-#pragma unroll
-        for (int c = 0; c < 3; ++c)
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const cpx<float> e = dag ? cj(u[3 * d + c]) : u[3 * c + d];
-                lp[((long)(p - 1) * 9 + 3 * c + d) * g.V + xl] = pack2(f.ph * e.re, f.ph * e.im);
-            }
     }
 }
 
@@ -1506,11 +1335,6 @@ cudaError_t launch_ptc_loss_delta(const void* aL, const void* e, void* delta, co
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     sum_partials<<<1, 256, 0, st>>>(partial, nb, out);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_ptc_links(const PtcGeom& g, uint32_t* lp, cudaStream_t st) {
-    ptc_links<<<(unsigned)((g.V + 255) / 256), 256, 0, st>>>(g, lp);
     return cudaGetLastError();
 }
 
