@@ -134,8 +134,14 @@ tm_status tm_clover_export(tm_ctx* ctx, int parity, double* out, void* stream);
 /* Bytes of one native odd-site field: nflavour 1 (light) or 2 (heavy). */
 tm_status tm_field_bytes(const tm_ctx* ctx, tm_prec prec, int nflavour, size_t* bytes);
 /* canonical FP64 <-> native (device).  The canonical pointer may be a host
- * pointer (detected; copied through a library-owned device staging buffer, and
- * the call then synchronises `stream`) or a device pointer.  16-byte aligned. */
+ * pointer or a device pointer.  16-byte aligned.  A host pointer is copied
+ * through one of three library-owned device staging buffers per direction:
+ *   - pageable host memory: the call synchronises `stream` before returning;
+ *   - pinned host memory (cudaMallocHost / cudaHostRegister): the call is
+ *     stream-ordered like the device case; the caller keeps the source unchanged
+ *     (import) or leaves the destination unread (export) until `stream` has
+ *     passed the call, so imports and exports on different streams can overlap
+ *     an operator running on a third. */
 tm_status tm_field_import(tm_ctx* ctx, tm_prec prec, int nflavour, void* dst_native,
                           const double* src_canonical, void* stream);
 tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_canonical,
@@ -166,7 +172,9 @@ tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, 
 
 /* out = op(in), native fields of precision prec on the device (eq:hQpm / eq:hQh).
  * Light ops take nflavour-1 fields, heavy ops nflavour-2 fields.  out != in.
- * Returns TM_ERR_STALE if the clover term predates the gauge field. */
+ * Returns TM_ERR_STALE if the clover term predates the gauge field.  Operator
+ * calls on one context share its intermediate fields: issue them on one stream
+ * (field imports and exports may run on others). */
 tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,
                         void* stream);
 

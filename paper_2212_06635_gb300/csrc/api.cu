@@ -71,6 +71,39 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// pinned (page-locked or registered) host memory: copies from / to it stay
+// asynchronous, so the field calls need not synchronise
+static bool is_pinned_host(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+// next staging buffer of a ring, ordered after the work that last used it
+static tm_status io_slot(tm_ctx::IoRing& r, size_t bytes, cudaStream_t st, int* slot) {
+    if (r.bytes < bytes) {
+        for (int k = 0; k < tm_ctx::IoRing::N; ++k) {
+            if (r.free[k]) CK(cudaEventSynchronize(r.free[k]));
+            cudaFree(r.buf[k]);
+            r.buf[k] = nullptr;
+        }
+        r.bytes = 0;
+        for (int k = 0; k < tm_ctx::IoRing::N; ++k) {
+            CK(cudaMalloc(&r.buf[k], bytes));
+            if (!r.free[k]) CK(cudaEventCreateWithFlags(&r.free[k], cudaEventDisableTiming));
+        }
+        r.bytes = bytes;
+    }
+    const int k = r.next;
+    r.next = (r.next + 1) % tm_ctx::IoRing::N;
+    CK(cudaStreamWaitEvent(st, r.free[k], 0));   // no-op until the event is first recorded
+    *slot = k;
+    return TM_OK;
+}
+
 static tm_status ws_get(tm_ctx* c, int id, size_t bytes, void** out) {
     auto it = c->ws.find(id);
     if (it != c->ws.end() && it->second.second >= bytes) {
@@ -143,6 +176,14 @@ extern "C" tm_status tm_destroy(tm_ctx* c) {
     cudaFree(c->partial); cudaFree(c->counter); cudaFree(c->ctl); cudaFree(c->ms); cudaFree(c->d_scal);
     cudaFreeHost(c->h_ctl); cudaFreeHost(c->h_ms); cudaFreeHost(c->h_scal);
     for (auto& kv : c->ws) cudaFree(kv.second.first);
+    for (tm_ctx::IoRing* r : {&c->io_in, &c->io_out})
+        for (int k = 0; k < tm_ctx::IoRing::N; ++k) {
+            if (r->free[k]) {
+                cudaEventSynchronize(r->free[k]);
+                cudaEventDestroy(r->free[k]);
+            }
+            cudaFree(r->buf[k]);
+        }
     if (c->sstream) cudaStreamDestroy(c->sstream);
     delete c;
     return TM_OK;
@@ -446,11 +487,13 @@ extern "C" tm_status tm_field_import(tm_ctx* c, tm_prec prec, int nf, void* dst,
         return TM_OK;
     }
     const size_t bytes = sizeof(double) * 24 * nf * c->vh;
-    void* stage = nullptr;
-    CKS(ws_get(c, WS_STAGE_IO, bytes, &stage));
+    int k = 0;
+    CKS(io_slot(c->io_in, bytes, st, &k));
+    void* stage = c->io_in.buf[k];
     CK(cudaMemcpyAsync(stage, src, bytes, cudaMemcpyHostToDevice, st));
     CK(import_any(prec, nf, dst, reinterpret_cast<const double*>(stage), c->vh, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaEventRecord(c->io_in.free[k], st));
+    if (!is_pinned_host(src)) CK(cudaStreamSynchronize(st));
     return TM_OK;
 }
 
@@ -465,11 +508,13 @@ extern "C" tm_status tm_field_export(tm_ctx* c, tm_prec prec, int nf, double* ds
         return TM_OK;
     }
     const size_t bytes = sizeof(double) * 24 * nf * c->vh;
-    void* stage = nullptr;
-    CKS(ws_get(c, WS_STAGE_IO, bytes, &stage));
+    int k = 0;
+    CKS(io_slot(c->io_out, bytes, st, &k));
+    void* stage = c->io_out.buf[k];
     CK(export_any(prec, nf, reinterpret_cast<double*>(stage), src, c->vh, st));
     CK(cudaMemcpyAsync(dst, stage, bytes, cudaMemcpyDeviceToHost, st));
-    CK(cudaStreamSynchronize(st));
+    CK(cudaEventRecord(c->io_out.free[k], st));
+    if (!is_pinned_host(dst)) CK(cudaStreamSynchronize(st));
     return TM_OK;
 }
 

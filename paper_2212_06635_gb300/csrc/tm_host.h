@@ -48,6 +48,17 @@ struct tm_ctx {
 
     std::map<int, std::pair<void*, size_t>> ws;   // workspace buffers by id
 
+    // host-buffer staging of tm_field_import / tm_field_export: a ring of device
+    // buffers per direction, each released by an event recorded after its last use,
+    // so calls with pinned host memory on different streams can overlap
+    struct IoRing {
+        static constexpr int N = 3;
+        void* buf[N] = {};
+        cudaEvent_t free[N] = {};
+        size_t bytes = 0;
+        int next = 0;
+    } io_in, io_out;
+
     // stencil kernel variant per [storage precision][flavours - 1][pass]:
     // 0 = direct (registers), 1 = shared-memory staged; set by tm_autotune / tm_set_tuning
     int variant[4][2][2] = {};

@@ -246,3 +246,53 @@ def test_cg_on_W_hat_normal_operator():
         assert S.rel_residual(A, from_dev(x, b.shape), b) <= 1.05e-10
     finally:
         lat.close()
+
+
+def test_pinned_host_fields_are_stream_ordered_and_overlap():
+    """Imports and exports with pinned host buffers on their own streams, the
+    operator on a third, several steps in flight (the bench's end-to-end loop):
+    every result equals the synchronous device-pointer path."""
+    import torch
+    dims = (4, 4, 4, 8)
+    op, lat = _lat(dims, 1700)
+    tm = lat.tm
+    try:
+        rhs = [F.odd_spinor(dims, 2700 + k) for k in range(5)]
+        ref = []
+        for b in rhs:
+            fi = lat.native(tm.TM_F32, 1)
+            fo = lat.native(tm.TM_F32, 1)
+            tm.tm_field_import(lat.ctx, tm.TM_F32, 1, fi, to_dev(b))
+            tm.tm_apply_Mhat(lat.ctx, tm.TM_MDAGM, tm.TM_F32, fo, fi)
+            o = to_dev(np.zeros_like(b))
+            tm.tm_field_export(lat.ctx, tm.TM_F32, 1, o, fo)
+            torch.cuda.synchronize()
+            ref.append(from_dev(o, b.shape))
+        hin = [torch.from_numpy(b.view(np.float64).reshape(-1).copy()).pin_memory() for b in rhs]
+        hout = [torch.zeros_like(h).pin_memory() for h in hin]
+        fins = [lat.native(tm.TM_F32, 1) for _ in range(2)]
+        fouts = [lat.native(tm.TM_F32, 1) for _ in range(2)]
+        s_in, s_op, s_out = torch.cuda.Stream(), torch.cuda.Stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_op = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
+        for k in range(len(rhs)):
+            i = k % 2
+            if k >= 2:
+                s_in.wait_event(ev_op[i])
+            tm.tm_field_import(lat.ctx, tm.TM_F32, 1, fins[i], hin[k], stream=s_in)
+            ev_in[i].record(s_in)
+            s_op.wait_event(ev_in[i])
+            if k >= 2:
+                s_op.wait_event(ev_out[i])
+            tm.tm_apply_Mhat(lat.ctx, tm.TM_MDAGM, tm.TM_F32, fouts[i], fins[i], stream=s_op)
+            ev_op[i].record(s_op)
+            s_out.wait_event(ev_op[i])
+            tm.tm_field_export(lat.ctx, tm.TM_F32, 1, hout[k], fouts[i], stream=s_out)
+            ev_out[i].record(s_out)
+        torch.cuda.synchronize()
+        for k, b in enumerate(rhs):
+            got = hout[k].numpy().view(np.complex128).reshape(b.shape)
+            assert np.array_equal(got, ref[k])
+    finally:
+        lat.close()
