@@ -125,7 +125,7 @@ enum WsId {
     WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
     WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO, WS_TUNE,
-    WS_FCG_Z, WS_FCG_PO, WS_FCG_QO,
+    WS_FCG_Z,
     WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
 };
 
@@ -1877,7 +1877,7 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     const long vh = c->vh;
     const int nb = nblk(vh, BLAS_BS);
     const size_t s64 = spinor_bytes(P64, 12, vh), s32 = spinor_bytes(P32, 12, vh);
-    void *x64, *b64, *r64, *ax64, *te64, *mid64, *xs, *rs, *z, *p, *q, *po, *qo, *te, *mid;
+    void *x64, *b64, *r64, *ax64, *te64, *mid64, *xs, *rs, *z, *p, *q, *te, *mid;
     CKS(ws_get(c, WS_X64, s64, &x64));
     CKS(ws_get(c, WS_B64, s64, &b64));
     CKS(ws_get(c, WS_R64, s64, &r64));
@@ -1891,8 +1891,6 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     CKS(ws_get(c, WS_TE_S, s32, &te));
     CKS(ws_get(c, WS_MID_S, s32, &mid));
     CKS(ws_get(c, WS_FCG_Z, s32, &z));
-    CKS(ws_get(c, WS_FCG_PO, s32, &po));
-    CKS(ws_get(c, WS_FCG_QO, s32, &qo));
     CKS(stage_in(c, 1, b, WS_STAGE_B, b64, st));
     CKS(stage_in(c, 1, x, WS_STAGE_X, x64, st));
     const double tol = sp->tol > 0 ? sp->tol : 1e-10;
@@ -1932,10 +1930,10 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
             if (first) {
                 CK(cudaMemcpyAsync(p, z, s32, cudaMemcpyDeviceToDevice, st));
             } else {
+                // p = z + beta p_old in place, beta = -<q_old, z> / <p_old, q_old>; p and q
+                // still hold the previous direction and its image here
                 double qr, qi;
-                CKS(cdot(qo, z, &qr, &qi));
-                // p = z + beta p_old, beta = -<q_old, z> / <p_old, q_old>
-                CK(cudaMemcpyAsync(p, po, s32, cudaMemcpyDeviceToDevice, st));
+                CKS(cdot(q, z, &qr, &qi));
                 CK(launch_cxpay32(p, z, -qr / pq_old, -qi / pq_old, vh, st));
             }
             // q = A p with <p, q> = ||Q p||^2 fused
@@ -1948,8 +1946,6 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
             const double ar = pr / pq, ai = pi / pq;
             CK(launch_caxpy32(xs, p, ar, ai, vh, st));
             CK(launch_caxpy32(rs, q, -ar, -ai, vh, st));
-            CK(cudaMemcpyAsync(po, p, s32, cudaMemcpyDeviceToDevice, st));
-            CK(cudaMemcpyAsync(qo, q, s32, cudaMemcpyDeviceToDevice, st));
             pq_old = pq;
             first = false;
             ++its;
