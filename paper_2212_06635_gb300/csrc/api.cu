@@ -1462,6 +1462,10 @@ struct tm_ptc {
     int nsm = 0;
     int* derr = nullptr;       // set by a layer kernel whose tensor-core wait ran out of its bound
     void* zmix = nullptr;      // per-path mixed fields of the layers with one output channel (9 channels)
+    uint32_t* lp = nullptr;    // FP16 transport links [8][9][V] of lp_ctx at gauge generation lp_gen
+    const tm_ctx* lp_ctx = nullptr;
+    long lp_gen = -1;
+    double lp_bct = 0.0;
 };
 
 static size_t ptc_nw(const tm_ptc* n, int l) { return (size_t)9 * n->ch[l + 1] * n->ch[l] * 16; }
@@ -1518,6 +1522,9 @@ static void ptc_free_acts(tm_ptc* n) {
     for (auto& d : n->del) { cudaFree(d); d = nullptr; }
     cudaFree(n->dpart); n->dpart = nullptr;
     cudaFree(n->zmix); n->zmix = nullptr;
+    cudaFree(n->lp); n->lp = nullptr;
+    n->lp_ctx = nullptr;
+    n->lp_gen = -1;
     cudaFree(n->e32); cudaFree(n->r32); cudaFree(n->tmp32[0]); cudaFree(n->tmp32[1]);
     n->e32 = n->r32 = n->tmp32[0] = n->tmp32[1] = nullptr;
     n->V = 0;
@@ -1548,6 +1555,7 @@ static tm_status ptc_buffers(tm_ptc* n, const tm_ctx* c) {
     for (auto& d : n->del) CK(cudaMalloc(&d, (size_t)PTC_MAXC * 3 * 16 * V));
     CK(cudaMalloc(&n->dpart, sizeof(double) * ((V + 255) / 256)));
     CK(cudaMalloc(&n->zmix, (size_t)9 * 3 * 16 * V));
+    CK(cudaMalloc(&n->lp, (size_t)8 * 9 * 4 * V));
     const size_t s32 = spinor_bytes(P32, 12, c->vh);
     CK(cudaMalloc(&n->e32, s32));
     CK(cudaMalloc(&n->r32, s32));
@@ -1565,6 +1573,7 @@ static PtcGeom ptc_geom(const tm_ctx* c) {
     g.bc_t = (float)c->params.bc_t;
     g.gauge[0] = c->gaugeP[PF16][0];
     g.gauge[1] = c->gaugeP[PF16][1];
+    g.lp = nullptr;
     return g;
 }
 
@@ -1646,9 +1655,25 @@ extern "C" tm_status tm_ptc_init(tm_ptc* n, double scale, double noise, unsigned
     return tm_ptc_set_weights(n, w.data());
 }
 
+// geometry of c with the network's transport-link field, rebuilt when the
+// context, its gauge field or its time boundary phase changed
+static tm_status ptc_geom_links(tm_ptc* n, tm_ctx* c, cudaStream_t st, PtcGeom* out) {
+    PtcGeom g = ptc_geom(c);
+    if (n->lp_ctx != c || n->lp_gen != c->gauge_gen || n->lp_bct != c->params.bc_t) {
+        CK(launch_ptc_links(g, n->lp, st));
+        n->lp_ctx = c;
+        n->lp_gen = c->gauge_gen;
+        n->lp_bct = c->params.bc_t;
+    }
+    g.lp = n->lp;
+    *out = g;
+    return TM_OK;
+}
+
 // z (FP32 native odd) = N(r) (FP32 native odd); activations kept in n->act
 static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaStream_t st) {
-    const PtcGeom g = ptc_geom(c);
+    PtcGeom g;
+    CKS(ptc_geom_links(n, c, st, &g));
     CK(launch_ptc_embed_odd(P32, r, n->act[0], g, st));
     for (int l = 0; l < n->L; ++l)
         CK(launch_ptc_layer(n->ch[l], n->ch[l + 1], g, n->act[l], n->act[l + 1], n->wf[l], n->nsm, n->derr, n->zmix,
@@ -1659,7 +1684,8 @@ static tm_status ptc_forward(tm_ptc* n, tm_ctx* c, void* z, const void* r, cudaS
 
 // loss of (r, e) with activations from ptc_forward(r); gradients accumulate into G (scaled)
 static tm_status ptc_backward(tm_ptc* n, tm_ctx* c, const void* e, float scale, cudaStream_t st) {
-    const PtcGeom g = ptc_geom(c);
+    PtcGeom g;
+    CKS(ptc_geom_links(n, c, st, &g));
     CK(launch_ptc_loss_delta(n->act[n->L], e, n->del[0], g, n->dscal + 0, n->dpart, n->dscal + 1, st));
     int cur = 0;
     for (int l = n->L - 1; l >= 0; --l) {

@@ -295,6 +295,44 @@ __device__ __forceinline__ void tc_locate(const PtcGeom& g, const TcSite& s, int
     f.flags = fwd ? 1 : 5;
 }
 
+// As tc_locate, but the link comes from the transport-link field g.lp: 9 FP16
+// (re, im) words of M (daggered and phased already) at the site itself.
+struct TcUnitL {
+    int y;
+    uint32_t lw[9];
+    int flags;   // bit 0 valid, bit 1 identity path
+};
+
+__device__ __forceinline__ void tc_locate_l(const PtcGeom& g, const TcSite& s, int p, TcUnitL& f) {
+    f.flags = 0;
+    if (p >= 9 || !s.valid) return;
+    f.y = s.x;
+    if (p == 0) {
+        f.flags = 3;
+        return;
+    }
+    const int mu = (p - 1) & 3;
+    const int L = mu == 0 ? g.X : (mu == 1 ? g.Y : (mu == 2 ? g.Z : g.T));
+    const int st = mu == 0 ? 1 : (mu == 1 ? g.X : (mu == 2 ? g.X * g.Y : g.X * g.Y * g.Z));
+    const int cm = s.c[mu];
+    if (p <= 4) f.y = (cm + 1 == L) ? s.x - (L - 1) * st : s.x + st;
+    else f.y = (cm == 0) ? s.x + (L - 1) * st : s.x - st;
+    const uint32_t* base = g.lp + (long)(p - 1) * 9 * g.V + s.x;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) f.lw[k] = __ldg(base + (long)k * g.V);
+    f.flags = 1;
+}
+
+// link words of a unit as broadcast pairs for paired FP32 FMAs: (Re M, Re M), (Im M, Im M)
+__device__ __forceinline__ void tc_pairs_l(const TcUnitL& f, float2 (&mr)[9], float2 (&mi)[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const float2 h = h2f2<PF16>(f.lw[k]);
+        mr[k] = make_float2(h.x, h.x);
+        mi[k] = make_float2(h.y, h.y);
+    }
+}
+
 __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
 }
@@ -531,9 +569,9 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         const uint32_t raw_base = smem_addr(Raw) + 16 * tid;
         const uint4* rawp = reinterpret_cast<const uint4*>(Raw) + tid;
         TcSite site = tc_site(g, (long)blockIdx.x * TC_SITES + r), nsite = site;
-        TcUnit nxt;
+        TcUnitL nxt;
         nxt.flags = 0;
-        if (pi < S::NPATH) tc_locate(g, site, pi, nxt);
+        if (pi < S::NPATH) tc_locate_l(g, site, pi, nxt);
         if (nxt.flags & 1) {
 #pragma unroll
             for (int k = 0; k < S::CPG; ++k)
@@ -545,14 +583,14 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
         for (long tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++j) {
             for (int stg = 0; stg < S::NSTG; ++stg, ++u) {
                 const int buf = u % TC_STAGES;
-                const TcUnit cur = nxt;
+                const TcUnitL cur = nxt;
                 {   // this thread's next stage (possibly the next tile's first)
                     const bool last = stg + 1 == S::NSTG;
                     const long nt = last ? tile + gridDim.x : tile;
                     const int np = (last ? 0 : (stg + 1) * S::NPS) + pi;
                     if (last) nsite = tc_site(g, nt * TC_SITES + r);
                     nxt.flags = 0;
-                    if (nt < ntiles && np < S::NPATH) tc_locate(g, nsite, np, nxt);
+                    if (nt < ntiles && np < S::NPATH) tc_locate_l(g, nsite, np, nxt);
                 }
                 // every lane of a warp runs the same iterations, so the vote keeps the
                 // warp together on the way out and at the epilogue's aligned loads
@@ -563,12 +601,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                 }
                 cp_async_wait_all();
                 float2 mr[9], mi[9];
-                if ((cur.flags & 3) == 1) {
-                    cpx<float> lk[9];
-                    tc_link(cur, lk);
-                    if (cur.flags & 4) tc_link_pairs<true>(lk, mr, mi);
-                    else tc_link_pairs<false>(lk, mr, mi);
-                }
+                if ((cur.flags & 3) == 1) tc_pairs_l(cur, mr, mi);
                 const bool copy = (cur.flags & 2) != 0;
                 uint8_t* img = Asm + (long)buf * S::A_STAGE + (long)pi * 3 * S::A_COL + (r >> 3) * (128 * S::KCH) +
                                (r & 7) * 16;
@@ -580,7 +613,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                         for (int q = 0; q < 3; ++q) a[q] = rawp[(k * 3 + q) * TC_PT];
                         uint8_t* dst = img + (b0 + k) * 128;
                         if (copy) tc_copy_channel<S::A_COL>(a, dst);
-                        else tc_transport_channel<S::A_COL>(a, mr, mi, cur.ph, dst);
+                        else tc_transport_channel<S::A_COL>(a, mr, mi, 1.f, dst);   // phase in the link
                     }
                     // the slot's current words are consumed: bring the next stage's
                     if (nxt.flags & 1) {
@@ -620,6 +653,33 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
     }
 }
 
+// Transport links of the eight hop paths as FP16 (re, im) pairs in lexicographic
+// site order: lp[(p - 1) * 9 + 3 c + d][x] = ph M[c][d], M = U_mu(x) for
+// p = 1..4 (mu = p - 1) and U_mu(x - mu)^dagger for p = 5..8, ph the time
+// boundary phase of the hop.  The transport kernels read the link of a (site,
+// path) here (9 loads) instead of rebuilding it from the 12-real even-odd links;
+// the field is rebuilt whenever the gauge field or the boundary phase changes.
+__global__ void __launch_bounds__(256) ptc_links(PtcGeom g, uint32_t* __restrict__ lp) {
+    const long xl = (long)blockIdx.x * 256 + threadIdx.x;
+    if (xl >= g.V) return;
+    const TcSite site = tc_site(g, xl);
+#pragma unroll 1
+    for (int p = 1; p < 9; ++p) {
+        TcUnit f;
+        tc_locate(g, site, p, f);
+        cpx<float> u[9];
+        tc_link(f, u);
+        const bool dag = (f.flags & 4) != 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const cpx<float> e = dag ? cj(u[3 * d + c]) : u[3 * c + d];
+                lp[((long)(p - 1) * 9 + 3 * c + d) * g.V + xl] = f2h2<PF16>(f.ph * e.re, f.ph * e.im);
+            }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Layers with one output channel and C_in > 1 (8->1, 4->1, 2->1) mix first:
 // the spin-space weights commute with the colour-space transport, so
@@ -645,11 +705,14 @@ __global__ void __launch_bounds__(256) ptc_tsum(PtcGeom g, const uint4* __restri
     }
 #pragma unroll 1
     for (int p = 1; p < 9; ++p) {
-        TcUnit f;
-        tc_locate(g, site, p, f);
-        cpx<float> u[9];
-        tc_link(f, u);
-        const bool dag = (f.flags & 4) != 0;
+        TcUnitL f;
+        tc_locate_l(g, site, p, f);
+        cpx<float> u[9];   // M of the path: daggered and phased already
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            const float2 h = h2f2<PF16>(f.lw[k]);
+            u[k] = C(h.x, h.y);
+        }
         cpx<float> v[12];
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -665,13 +728,8 @@ __global__ void __launch_bounds__(256) ptc_tsum(PtcGeom g, const uint4* __restri
         for (int sp = 0; sp < 4; ++sp)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                cpx<float> t = C(0.f, 0.f);
 #pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    if (dag) cfma_cj(t, u[3 * d + c], v[3 * sp + d]);
-                    else cfma(t, u[3 * c + d], v[3 * sp + d]);
-                }
-                acc[3 * sp + c] = acc[3 * sp + c] + f.ph * t;
+                for (int d = 0; d < 3; ++d) cfma(acc[3 * sp + c], u[3 * c + d], v[3 * sp + d]);
             }
     }
 #pragma unroll
@@ -854,7 +912,7 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
         // site coordinates change once per site block (every NG stages)
         TcSite lsite;
         long lsb = -1;
-        auto locate = [&](int u, TcUnit& f) {
+        auto locate = [&](int u, TcUnitL& f) {
             f.flags = 0;
             if (u >= nst) return;
             const int grp = u % S::NG;
@@ -863,9 +921,9 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
                 lsite = tc_site(g, sb * WG_S + j);
                 lsb = sb;
             }
-            tc_locate(g, lsite, grp * S::PPM + ps, f);
+            tc_locate_l(g, lsite, grp * S::PPM + ps, f);
         };
-        TcUnit nxt;
+        TcUnitL nxt;
         locate(0, nxt);
         if (nxt.flags & 1) {
 #pragma unroll
@@ -874,7 +932,7 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
         cp_async_commit();
         for (int u = 0; u < nst; ++u) {
             const int buf = u & 1, grp = u % S::NG, sbi = u / S::NG;
-            const TcUnit cur = nxt;
+            const TcUnitL cur = nxt;
             locate(u + 1, nxt);
             const bool w = u < 2 || mbar_wait(empty + buf, ((u >> 1) - 1) & 1, abort_flag);
             if (!__all_sync(0xffffffffu, w)) { ok = false; break; }
@@ -908,13 +966,8 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
                 for (int q = 0; q < 3; ++q) a[q] = rawp[q * WG_PT];
                 float2 mr[9], mi[9];
                 const bool copy = (cur.flags & 2) != 0;
-                if (!copy) {
-                    cpx<float> lk[9];
-                    tc_link(cur, lk);
-                    if (cur.flags & 4) tc_link_pairs<true>(lk, mr, mi);
-                    else tc_link_pairs<false>(lk, mr, mi);
-                }
-                wg_transport_unit(a, mr, mi, cur.ph, copy, img, j);
+                if (!copy) tc_pairs_l(cur, mr, mi);
+                wg_transport_unit(a, mr, mi, 1.f, copy, img, j);   // phase in the link
             } else {
                 // no site or no path: zero rows (an earlier stage may have left values)
 #pragma unroll
@@ -1335,6 +1388,11 @@ cudaError_t launch_ptc_loss_delta(const void* aL, const void* e, void* delta, co
     cudaError_t err = cudaGetLastError();
     if (err != cudaSuccess) return err;
     sum_partials<<<1, 256, 0, st>>>(partial, nb, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ptc_links(const PtcGeom& g, uint32_t* lp, cudaStream_t st) {
+    ptc_links<<<(unsigned)((g.V + 255) / 256), 256, 0, st>>>(g, lp);
     return cudaGetLastError();
 }
 

@@ -12,6 +12,8 @@ struct PtcGeom {
     long V, vh;
     float bc_t;
     const void* gauge[2];   // FP16 native links per parity
+    const uint32_t* lp;     // transport links of paths 1..8, FP16 (re, im) pairs [8][9][V]
+                            // (U^dagger for backward paths, time boundary phase included)
 };
 
 // one layer on the tensor cores; *err is set to 1 if a wait on the tensor cores ran
@@ -22,6 +24,8 @@ cudaError_t launch_ptc_layer(int cin, int cout, const PtcGeom& g, const void* in
                              int nsm, int* err, void* zbuf, cudaStream_t st);
 // weight gradient of one layer into grad (scaled, accumulated); partial holds
 // 9 * 4096 floats per block, min(nsm, sites / 32) blocks
+// lp[(p - 1) * 9 + 3 c + d][x] from the FP16 even-odd links of g
+cudaError_t launch_ptc_links(const PtcGeom& g, uint32_t* lp, cudaStream_t st);
 cudaError_t launch_ptc_wgrad(int cin, int cout, const PtcGeom& g, const void* in, const void* delta, float* partial,
                              int nsm, float2* grad, float scale, int* err, cudaStream_t st);
 cudaError_t launch_ptc_embed_weights(const float2* W, int cin, int cout, void* fwd, void* adj, cudaStream_t st);
