@@ -349,28 +349,15 @@ __device__ __forceinline__ void tc_link(const TcUnit& f, cpx<float> (&u)[9]) {
     su3_third_row(u);
 }
 
-// Link of a unit as broadcast pairs for paired FP32 FMAs: mr[c][d] = (Re M, Re M),
-// mi[c][d] = (Im M, Im M) with M = U, or U^dagger for a backward path.
-template <bool DAG>
-__device__ __forceinline__ void tc_link_pairs(const cpx<float> (&u)[9], float2 (&mr)[9], float2 (&mi)[9]) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c)
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            const cpx<float> e = DAG ? cj(u[3 * d + c]) : u[3 * c + d];
-            mr[3 * c + d] = make_float2(e.re, e.re);
-            mi[3 * c + d] = make_float2(e.im, e.im);
-        }
-}
-
 // One channel of a unit: 12 activation words (complex (spin s, colour c) is
 // word 3 s + c) -> one 16-byte chunk per colour of the A images at img (4 spins
-// as BF16 (re, im) pairs): t = ph M v.  Two spins share each paired FMA:
+// as BF16 (re, im) pairs): t = M v, M the path's link with its dagger and phase
+// already applied.  Two spins share each paired FMA:
 //   Re t = sum_d Re M Re v + Im M (-Im v),  Im t = sum_d Re M Im v + Im M Re v,
 // each lane in the same order as the scalar form.
 template <int A_COL>
 __device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], const float2 (&mr)[9],
-                                                     const float2 (&mi)[9], float ph, uint8_t* img) {
+                                                     const float2 (&mi)[9], uint8_t* img) {
     const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
                             a[2].x, a[2].y, a[2].z, a[2].w};
     uint32_t wd[3][4];
@@ -394,10 +381,6 @@ __device__ __forceinline__ void tc_transport_channel(const uint4 (&a)[3], const 
                 tr = __ffma2_rn(mi[3 * c + d], nvi[d], tr);
                 ti = __ffma2_rn(mr[3 * c + d], vi[d], ti);
                 ti = __ffma2_rn(mi[3 * c + d], vr[d], ti);
-            }
-            if (ph != 1.f) {
-                tr = make_float2(ph * tr.x, ph * tr.y);
-                ti = make_float2(ph * ti.x, ph * ti.y);
             }
             wd[c][2 * h] = pack2(tr.x, ti.x);
             wd[c][2 * h + 1] = pack2(tr.y, ti.y);
@@ -613,7 +596,7 @@ __global__ void __launch_bounds__(TC_BS, 1) ptc_layer_tc(PtcGeom g, const uint4*
                         for (int q = 0; q < 3; ++q) a[q] = rawp[(k * 3 + q) * TC_PT];
                         uint8_t* dst = img + (b0 + k) * 128;
                         if (copy) tc_copy_channel<S::A_COL>(a, dst);
-                        else tc_transport_channel<S::A_COL>(a, mr, mi, 1.f, dst);   // phase in the link
+                        else tc_transport_channel<S::A_COL>(a, mr, mi, dst);
                     }
                     // the slot's current words are consumed: bring the next stage's
                     if (nxt.flags & 1) {
@@ -788,7 +771,7 @@ __device__ __forceinline__ void tmem_wait_ld1(uint32_t (&a)[8]) {
 // One (site, path, channel) unit: transport (or copy for the identity path) and
 // write its 8 rows (2 t + ri) for each colour's K index as a 16-byte BF16 chunk.
 __device__ __forceinline__ void wg_transport_unit(const uint4 (&a)[3], const float2 (&mr)[9], const float2 (&mi)[9],
-                                                  float ph, bool copy, uint8_t* img, int j) {
+                                                  bool copy, uint8_t* img, int j) {
     const uint32_t w[12] = {a[0].x, a[0].y, a[0].z, a[0].w, a[1].x, a[1].y, a[1].z, a[1].w,
                             a[2].x, a[2].y, a[2].z, a[2].w};
     uint32_t wd[3][4];   // [colour][spin]: (re, im) BF16
@@ -818,10 +801,6 @@ __device__ __forceinline__ void wg_transport_unit(const uint4 (&a)[3], const flo
                     tr = __ffma2_rn(mi[3 * c + d], nvi[d], tr);
                     ti = __ffma2_rn(mr[3 * c + d], vi[d], ti);
                     ti = __ffma2_rn(mi[3 * c + d], vr[d], ti);
-                }
-                if (ph != 1.f) {
-                    tr = make_float2(ph * tr.x, ph * tr.y);
-                    ti = make_float2(ph * ti.x, ph * ti.y);
                 }
                 wd[c][2 * h] = pack2(tr.x, ti.x);
                 wd[c][2 * h + 1] = pack2(tr.y, ti.y);
@@ -967,7 +946,7 @@ __global__ void __launch_bounds__(WG_BS, 1) ptc_wgrad_tc(PtcGeom g, const uint4*
                 float2 mr[9], mi[9];
                 const bool copy = (cur.flags & 2) != 0;
                 if (!copy) tc_pairs_l(cur, mr, mi);
-                wg_transport_unit(a, mr, mi, 1.f, copy, img, j);   // phase in the link
+                wg_transport_unit(a, mr, mi, copy, img, j);
             } else {
                 // no site or no path: zero rows (an earlier stage may have left values)
 #pragma unroll
