@@ -5,6 +5,7 @@
 // dslash.cu, blas.cu and gauge.cu; this file only allocates, orders launches and
 // reads back solver control words.
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <cmath>
 #include <cstdarg>
@@ -137,7 +138,9 @@ extern "C" tm_status tm_create(tm_ctx** out, const int dims[4], int device) {
     for (int k = 0; k < 4; ++k)
         if (dims[k] < 2 || dims[k] % 2) return fail(TM_ERR_ARG, "tm_create: extent %d = %d must be even and >= 2", k, dims[k]);
     CK(cudaSetDevice(device));
+    static std::atomic<unsigned long long> next_uid{1};
     tm_ctx* c = new tm_ctx();
+    c->uid = next_uid.fetch_add(1);
     c->device = device;
     c->g.X = dims[0]; c->g.Y = dims[1]; c->g.Z = dims[2]; c->g.T = dims[3];
     c->vh = (long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
@@ -1462,8 +1465,8 @@ struct tm_ptc {
     int nsm = 0;
     int* derr = nullptr;       // set by a layer kernel whose tensor-core wait ran out of its bound
     void* zmix = nullptr;      // per-path mixed fields of the layers with one output channel (9 channels)
-    uint32_t* lp = nullptr;    // FP16 transport links [8][9][V] of lp_ctx at gauge generation lp_gen
-    const tm_ctx* lp_ctx = nullptr;
+    uint32_t* lp = nullptr;    // FP16 transport links [8][9][V] of context lp_uid at gauge generation lp_gen
+    unsigned long long lp_uid = 0;
     long lp_gen = -1;
     double lp_bct = 0.0;
 };
@@ -1523,7 +1526,7 @@ static void ptc_free_acts(tm_ptc* n) {
     cudaFree(n->dpart); n->dpart = nullptr;
     cudaFree(n->zmix); n->zmix = nullptr;
     cudaFree(n->lp); n->lp = nullptr;
-    n->lp_ctx = nullptr;
+    n->lp_uid = 0;
     n->lp_gen = -1;
     cudaFree(n->e32); cudaFree(n->r32); cudaFree(n->tmp32[0]); cudaFree(n->tmp32[1]);
     n->e32 = n->r32 = n->tmp32[0] = n->tmp32[1] = nullptr;
@@ -1656,12 +1659,12 @@ extern "C" tm_status tm_ptc_init(tm_ptc* n, double scale, double noise, unsigned
 }
 
 // geometry of c with the network's transport-link field, rebuilt when the
-// context, its gauge field or its time boundary phase changed
+// context (by its unique id), its gauge field or its time boundary phase changed
 static tm_status ptc_geom_links(tm_ptc* n, tm_ctx* c, cudaStream_t st, PtcGeom* out) {
     PtcGeom g = ptc_geom(c);
-    if (n->lp_ctx != c || n->lp_gen != c->gauge_gen || n->lp_bct != c->params.bc_t) {
+    if (n->lp_uid != c->uid || n->lp_gen != c->gauge_gen || n->lp_bct != c->params.bc_t) {
         CK(launch_ptc_links(g, n->lp, st));
-        n->lp_ctx = c;
+        n->lp_uid = c->uid;
         n->lp_gen = c->gauge_gen;
         n->lp_bct = c->params.bc_t;
     }

@@ -10,6 +10,9 @@
 #include "tm_kernels.h"
 
 struct tm_ctx {
+    // unique over the process lifetime (a destroyed context's address can be reused
+    // by the next one, so caches keyed on derived state use this id, not the pointer)
+    unsigned long long uid = 0;
     int device = 0;
     tmk::Geom g{};
     long vh = 0;

@@ -206,3 +206,29 @@ def test_bounded_wait_runs_out_and_leaves_the_context_usable():
     assert time.perf_counter() - t0 < 5.0
     x = torch.arange(1024, dtype=torch.float64, device="cuda")
     assert float((x * 2).sum()) == 1023 * 1024
+
+
+def test_network_follows_a_new_context_at_a_reused_address():
+    """The network caches a transport-link field per context.  Destroying a
+    context and creating the next one (whose address the allocator may reuse,
+    with the same gauge generation and boundary phase) must not leave the
+    previous gauge field's links in use: each forward pass matches the oracle on
+    its own field."""
+    dims = (4, 4, 2, 4)
+    chans = [1, 8, 1]
+    ws = P.random_weights(chans, 41, scale=1.0)
+    net = None
+    try:
+        for seed in (42, 43, 44):
+            u = F.gauge_field(dims, seed)
+            lat = Lat(u, dims, KAPPA, CSW, mu=MU)
+            try:
+                if net is None:
+                    net = _net(lat.tm, chans, ws)
+                r = F.odd_spinor(dims, seed + 100)
+                assert rel(_apply(lat.tm, lat, net, r), P.PTC(u, dims, ws).forward(r)) < FWD_TOL
+            finally:
+                lat.close()
+    finally:
+        if net is not None:
+            lat.tm.tm_ptc_destroy(net)
