@@ -232,3 +232,28 @@ def test_network_follows_a_new_context_at_a_reused_address():
     finally:
         if net is not None:
             lat.tm.tm_ptc_destroy(net)
+
+
+def test_gradients_alternating_between_two_live_contexts():
+    """One network used on two contexts in turn (A, B, A): the transport-link
+    field follows the context of each call, so every loss and gradient matches
+    the oracle on that context's own gauge field."""
+    dims = (4, 4, 2, 4)
+    chans = [1, 8, 1]
+    ws = P.random_weights(chans, 51, scale=1.0)
+    ua, ub = F.gauge_field(dims, 52), F.gauge_field(dims, 53)
+    la, lb = Lat(ua, dims, KAPPA, CSW, mu=MU), Lat(ub, dims, KAPPA, CSW, mu=MU)
+    tm = la.tm
+    net = _net(tm, chans, ws)
+    try:
+        r = F.odd_spinor(dims, 54)
+        e = F.odd_spinor(dims, 55)
+        for lat, u in ((la, ua), (lb, ub), (la, ua)):
+            L_ref, g_ref = P.PTC(u, dims, ws).grad(r, e)
+            L, g = tm.tm_ptc_grad(net, lat.ctx, to_dev(r), to_dev(e))
+            assert abs(L - L_ref) < FWD_TOL * L_ref
+            assert rel(g, np.concatenate([x.ravel() for x in g_ref])) < GRAD_TOL
+    finally:
+        tm.tm_ptc_destroy(net)
+        la.close()
+        lb.close()
