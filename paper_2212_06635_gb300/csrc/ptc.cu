@@ -7,18 +7,21 @@
 //   P = {1, +x,+y,+z,+t, -x,-y,-z,-t},  (T_{+mu} f)(x) = U_mu(x) f(x+mu),
 //   (T_{-mu} f)(x) = U_mu(x-mu)^dag f(x-mu),  W_p^{ab} a complex 4x4 spin matrix.
 // Because W acts on (channel, spin) and T on (site, colour), a tile of sites is
-// a real GEMM per path: with every complex number split into (re, im),
-//   Out[64 x 3S] += A_p[64 x 64] * V_p[64 x 3S],
-//   rows (re/im, a<8, s<4), K = (re/im, b<8, t<4), columns (site, colour),
-//   A_p = [[Re W, -Im W], [Im W, Re W]] (BF16), V_p = T_p in (BF16), FP32 accumulate.
-// The transport (gather of neighbour activations, SU(3) multiply) fills V_p in
-// shared memory; the mixing runs on the tcgen05 tensor cores with the
-// accumulators in tensor memory (ptc_layer_tc), and so does the weight gradient
-// (ptc_wgrad_tc).  Activations are BF16, layout
-// [channel][3 x 16-B vectors of 4 complex (spin, colour)][V] in lexicographic site
-// order.  The input gradient of a layer is the same layer run with the adjoint
-// weights W'_p = (W_{rev p})^H (T_p^dag = T_{rev p}); the weight gradient is the
-// site reduction G_p = sum_{x,c} delta(x) v_p(x)^H, again a BF16 tensor-core GEMM.
+// a real GEMM per path and colour: with every complex number split into (re, im),
+//   D[site][n] += A_p[site][k] B_p[n][k],
+//   n = 8 a + 2 s + re/im (output channel, spin), k = 8 b + 2 t + re/im (input),
+//   B_p the real embedding [[Re W, -Im W], [Im W, Re W]] (BF16), A_p = T_p in (BF16),
+//   FP32 accumulate.
+// The transport (gather of neighbour activations, SU(3) multiply with paired FP32
+// FMAs, links from a per-context FP16 transport-link field) fills A_p in shared
+// memory; the mixing runs on the tcgen05 tensor cores with the accumulators in
+// tensor memory (ptc_layer_tc).  Layers with one output channel mix first and
+// transport one channel per path (ptc_layer_tc<.., MIX> + ptc_tsum).  The weight
+// gradient G_p = sum_{x,c} delta(x) v_p(x)^H is the same product reduced over
+// sites, also on tcgen05 (ptc_wgrad_tc); the input gradient of a layer is the
+// layer run with the adjoint weights W'_p = (W_{rev p})^H (T_p^dag = T_{rev p}).
+// Activations are BF16, layout [channel][3 x 16-B vectors of 4 complex (spin,
+// colour)][V] in lexicographic site order.
 #include "tm_internal.h"
 #include "tm_kernels.h"
 #include "ptc.h"
