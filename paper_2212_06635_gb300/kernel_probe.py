@@ -48,6 +48,32 @@ def ptc_grad_probe(dims, reps):
         tm.tm_destroy(ctx)
 
 
+def ptc_fcg_probe(dims, iters):
+    """Flexible CG preconditioned by an untrained 1-8-8-8-1 network (identity
+    start), `iters` iterations on a seeded lattice: the launch sequence of the
+    PTC-FCG solve, without the training."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    u = F.gauge_field(dims, 1004)
+    b = F.odd_spinor(dims, 2004)
+    ctx = tm.tm_create(dims, 0)
+    net = tm.tm_ptc_create([1, 8, 8, 8, 1])
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, 0.1394265, 1.69, mu=0.00072)
+        tm.tm_ptc_init(net, 0.5, 0.02, 1)
+        bd = torch.from_numpy(b.view(np.float64).copy()).cuda()
+        x = torch.zeros_like(bd)
+        info = tm.tm_solve_fcg(ctx, tm.TM_MDAGM, net, tm.solve_params(tol=1e-14, maxiter=iters), x, bd, check=False)
+        print(f"dims {dims} PTC-FCG {info.iters} iterations in {info.seconds:.3f} s "
+              f"({1e3 * info.seconds / max(info.iters, 1):.2f} ms per iteration), "
+              f"{info.reliable_updates} reliable updates, status {info.status}")
+    finally:
+        tm.tm_ptc_destroy(net)
+        tm.tm_destroy(ctx)
+
+
 def ptc_probe(dims, reps):
     import torch
     from paper_2212_06635_gb300 import tm
@@ -91,6 +117,8 @@ def main():
     ap.add_argument("--ptc", action="store_true",
                     help="instead: apply a 1-8-8-8-1 PTC network (1 + reps) times; each application "
                          "launches its 4 layer kernels in order")
+    ap.add_argument("--ptc-fcg", type=int, default=0, metavar="ITERS",
+                    help="instead: ITERS iterations of flexible CG with an untrained 1-8-8-8-1 network")
     ap.add_argument("--ptc-grad", action="store_true",
                     help="instead: loss and gradient of a 1-8-8-8-1 PTC network on one pair, (1 + reps) times")
     a = ap.parse_args()
@@ -102,6 +130,8 @@ def main():
         return ptc_probe(dims, a.reps)
     if a.ptc_grad:
         return ptc_grad_probe(dims, a.reps)
+    if a.ptc_fcg:
+        return ptc_fcg_probe(dims, a.ptc_fcg)
     prec = PRECS[a.prec]
     nf = 2 if a.heavy else 1
     u = F.gauge_field(dims, 1001)
