@@ -91,7 +91,9 @@ typedef struct {
     double tol;          /* target FP64 true relative residual ||b - A x|| / ||b|| */
     int maxiter;         /* bound on Krylov iterations (all restarts together) */
     tm_prec sloppy;      /* storage precision of the inner iteration; TM_F64 = plain FP64 CG */
-    double delta;        /* reliable-update trigger: ||r_sloppy|| < delta * ||r_true_last|| */
+    double delta;        /* reliable-update trigger: ||r_sloppy|| < delta * ||r_true_last||;
+                            <= 0 selects a default of about sqrt(unit roundoff) of the
+                            sloppy storage: FP16 0.02, BF16 0.06, FP32 0.002 */
     int chunk;           /* iterations enqueued between two host checks (0 = default 16) */
     int use_graph;       /* capture the chunk in a CUDA graph and replay it */
     tm_prec refine;      /* tm_solve_multishift only: storage precision of the

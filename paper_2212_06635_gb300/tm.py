@@ -208,8 +208,9 @@ def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
     _check(lib.tm_apply_Mhat(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
 
 
-def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.1, chunk=16, use_graph=1, refine=TM_F64):
-    """refine: multishift refinement storage precision (TM_F64 = same as sloppy)."""
+def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.0, chunk=16, use_graph=1, refine=TM_F64):
+    """refine: multishift refinement storage precision (TM_F64 = same as sloppy);
+    delta <= 0: the library's reliable-update threshold for the sloppy precision."""
     return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph, refine)
 
 
