@@ -760,9 +760,12 @@ static tm_status get_ctl(tm_ctx* c, cudaStream_t st) {
 
 // r64 = b64 - (A + shift) x64, returns ||r64||^2
 template <int NF>
+// r = b - (A + shift) x and rr = ||r||^2 in FP64.  x_zero: x is known to be zero,
+// so A x = 0 without applying the operator (a zero initial guess).
 static tm_status true_residual(tm_ctx* c, tm_op op, double shift, void* x64, void* b64, void* r64, void* ax64,
-                               void* mid64, void* te64, cudaStream_t st, double* rr) {
-    CK((normal_op<P64, NF>(c, op, ax64, x64, mid64, te64, st, nullptr, FIN_NONE)));
+                               void* mid64, void* te64, cudaStream_t st, double* rr, bool x_zero = false) {
+    if (x_zero) CK(cudaMemsetAsync(ax64, 0, spinor_bytes(P64, 12 * NF, c->vh), st));
+    else CK((normal_op<P64, NF>(c, op, ax64, x64, mid64, te64, st, nullptr, FIN_NONE)));
     c->h_ctl->shift = shift;
     CK(cudaMemcpyAsync(&c->ctl->shift, &c->h_ctl->shift, sizeof(double), cudaMemcpyHostToDevice, st));
     CK((launch_residual64<12 * NF, 1>(vb1(c, r64, b64, ax64, x64, c->d_scal), nblk(c->vh, BLAS_BS), st)));
@@ -774,6 +777,15 @@ static tm_status norm2_dev(tm_ctx* c, const void* v, cudaStream_t st, double* ou
     CK((launch_norm2<P, NC, 1>(vb1(c, const_cast<void*>(v), nullptr, nullptr, nullptr, c->d_scal),
                                 nblk(c->vh, BLAS_BS), st)));
     return read_scalar(c, c->d_scal, out, st);
+}
+
+// whether a native FP64 field is exactly zero (||x||^2 == 0)
+template <int NF>
+static tm_status is_zero64(tm_ctx* c, const void* x64, cudaStream_t st, bool* zero) {
+    double xx = 0.0;
+    CKS((norm2_dev<P64, 12 * NF>(c, x64, st, &xx)));
+    *zero = xx == 0.0;
+    return TM_OK;
 }
 
 // One CG iteration in storage precision PS (x accumulated in PX):
@@ -841,7 +853,9 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
         return TM_OK;
     }
     double rr = 0;
-    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
+    bool x0 = false;
+    CKS(is_zero64<NF>(c, x64, st, &x0));
+    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, x0));
     const double target = tol * tol * bb;
     tm_status status = TM_OK;
     cudaGraphExec_t gexec = nullptr;
@@ -1258,7 +1272,9 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
         infos[q] = tm_solve_info{};
         if (!std::isfinite(bb[q])) { infos[q].status = TM_ERR_BREAKDOWN; done[q] = 1; continue; }
         if (!(bb[q] > 0)) { CK(cudaMemsetAsync(w[q].x64, 0, sz, st)); done[q] = 1; continue; }
-        CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
+        bool x0 = false;
+        CKS(is_zero64<1>(c, w[q].x64, st, &x0));
+        CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q], x0));
         if (rr[q] <= tol * tol * bb[q]) { done[q] = 1; continue; }
         if (PS != P64) {
             CK((launch_convert<PS, P64, NC, 1>(vb1(c, w[q].rs, r64), nblk(c->vh, BLAS_BS), st)));
@@ -1945,7 +1961,9 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     info->reliable_updates = 0;
     if (!std::isfinite(bb)) return fail(TM_ERR_BREAKDOWN, "tm_solve_fcg: right-hand side is not finite");
     double rr;
-    CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
+    bool x0 = false;
+    CKS(is_zero64<1>(c, x64, st, &x0));
+    CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr, x0));
     const double target = tol * tol * bb;
     std::memset(c->h_ctl, 0, sizeof(SolverCtl));
     CKS(put_ctl(c, st));
