@@ -52,11 +52,13 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
 // Resident blocks the compiler must fit per SM.  Both light 16-bit passes fit in
 // 96 registers (spilling at most 16 B; the even pass streams its inverse blocks
 // two rows at a time for this), which raises occupancy from 4 to 5 blocks of
-// 128 threads.  FP32, FP64 and heavy passes spill heavily at such bounds and keep
-// the default.
+// 128 threads.  The heavy 16-bit passes fit 4 blocks (128 registers; the even
+// pass streams its P blocks).  FP32 and FP64 passes spill heavily at such bounds
+// and keep the default.  Sweeps at 32^3x64 (light) and 24^3x48 (heavy) put the
+// optimum at these values.
 template <int P, int NF, int KIND>
 constexpr int dslash_min_blocks() {
-    return ((P == PF16 || P == PB16) && NF == 1) ? 5 : 1;
+    return (P == PF16 || P == PB16) ? (NF == 1 ? 5 : 4) : 1;
 }
 
 template <int P, int NF, int KIND, int NP, int BS>
@@ -117,7 +119,10 @@ __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash
                     for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
                 }
             } else {
-                // heavy: [[P, E],[E, P^+]] (sign +) or [[P^+, E],[E, P]] (sign -)
+                // heavy: [[P, E],[E, P^+]] (sign +) or [[P^+, E],[E, P]] (sign -).
+              if constexpr (P == P32) {
+                // FP32 (two resident blocks): the whole blocks are loaded at once, which
+                // keeps more loads in flight than streaming them
                 R e[72];
                 load_reals<P, 72>(pr.clov, pr.g.vh, i, 144, e);
 #pragma unroll
@@ -137,6 +142,50 @@ __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash
 #pragma unroll
                     for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
                 }
+              } else {
+                // 16-bit and FP64: the P block is streamed two rows (24 reals) at a time,
+                // each element serving both flavours (P v on one, P^+ v on the other); only
+                // this chirality's E block is loaded (40 reals from real 144 + 32 cb,
+                // aligned for every storage precision; the block starts 4 cb reals into
+                // them).  The 16-bit passes then fit four resident blocks.
+#pragma unroll
+                for (int cb = 0; cb < 2; ++cb) {
+                    cpx<R> vu[6], vd[6], wu[6], wd[6];
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        vu[j] = acc[0][2 * cb + j / 3][j % 3];
+                        vd[j] = acc[NF - 1][2 * cb + j / 3][j % 3];
+                        wu[j] = C((R)0, (R)0);
+                        wd[j] = C((R)0, (R)0);
+                    }
+#pragma unroll
+                    for (int rr = 0; rr < 3; ++rr) {
+                        R m[24];
+                        load_reals<P, 24>(pr.clov, pr.g.vh, i, 72 * cb + 24 * rr, m);
+#pragma unroll
+                        for (int r2 = 0; r2 < 2; ++r2) {
+                            const int r = 2 * rr + r2;
+#pragma unroll
+                            for (int j = 0; j < 6; ++j) {
+                                const cpx<R> e = C(m[2 * (6 * r2 + j)], m[2 * (6 * r2 + j) + 1]);
+                                if (pr.sign > 0) {
+                                    cfma(wu[r], e, vu[j]);       // P v_u
+                                    cfma_cj(wd[j], e, vd[r]);    // P^+ v_d
+                                } else {
+                                    cfma_cj(wu[j], e, vu[r]);    // P^+ v_u
+                                    cfma(wd[r], e, vd[j]);       // P v_d
+                                }
+                            }
+                        }
+                    }
+                    R e40[40];
+                    load_reals<P, 40>(pr.clov, pr.g.vh, i, 144 + 32 * cb, e40);
+                    herm6_mv_acc<R>(wu, e40 + 4 * cb, vd);
+                    herm6_mv_acc<R>(wd, e40 + 4 * cb, vu);
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
+                }
+              }
             }
         } else {
             // out = g5 [ (A + i tw g5 [tau3]) psi - eps tau1 psi - kappa^2 acc ]
