@@ -53,12 +53,14 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
 // 96 registers (spilling at most 16 B; the even pass streams its inverse blocks
 // two rows at a time for this), which raises occupancy from 4 to 5 blocks of
 // 128 threads.  The heavy 16-bit passes fit 4 blocks (128 registers; the even
-// pass streams its P blocks).  FP32 and FP64 passes spill heavily at such bounds
-// and keep the default.  Sweeps at 32^3x64 (light) and 24^3x48 (heavy) put the
-// optimum at these values.
+// pass streams its P blocks), the heavy FP32 odd pass 3 (168 registers, 8 B
+// spilled: 94.8 -> 78.1 us at 24^3x48).  The other FP32 and the FP64 passes keep
+// the default.  Sweeps at 32^3x64 (light) and 24^3x48 (heavy) put the optimum at
+// these values.
 template <int P, int NF, int KIND>
 constexpr int dslash_min_blocks() {
-    return (P == PF16 || P == PB16) ? (NF == 1 ? 5 : 4) : 1;
+    if (P == PF16 || P == PB16) return NF == 1 ? 5 : 4;
+    return (P == P32 && NF == 2 && KIND == K2_OE_LOCAL) ? 3 : 1;
 }
 
 template <int P, int NF, int KIND, int NP, int BS>
