@@ -15,4 +15,6 @@ Paper: "Twisted mass ensemble generation on GPU machines" (arXiv 2212.06635).
   solvers.py  CG, multishift CG (Sec. 4.2), power iteration, dense solves
   ptc.py      gauge-equivariant parallel-transport network preconditioner
               (not in the paper; parity of its training trajectory unpinned)
+  force.py    fermion-force outer products of the hopping term on every link
+              (the rational-approximation force step of Sec. 4.3)
 """
