@@ -332,6 +332,7 @@ def run_ours(args, rank, world, local_rank):
     if rank == 0 and not args.no_extra:
         extra["multishift_heavy_24x48"] = run_multishift(tm, args)
         extra["batch_uneven_24"] = run_batch(tm, args)
+        extra["force_outer_heavy_24x48"] = run_force(args, peak)
     if rank == 0 and not args.no_ptc:
         try:
             extra["ptc_fcg_48x96"] = run_ptc(tm, args)
@@ -458,6 +459,21 @@ def run_batch(tm, args):
     finally:
         for c in ctxs:
             tm.tm_destroy(c)
+    return out
+
+
+def run_force(args, peak):
+    """The rational-approximation force step on the heavy doublet at 24^3x48: the
+    outer products of 12 two-flavour field pairs (one per shift) on every link,
+    one tm_force_outer launch, fields in FP32 and in FP16 storage."""
+    from paper_2212_06635_gb300.kernel_probe import force_probe
+    dims = CFG.HEAVY_24.dims
+    out = {"lattice": list(dims), "pairs": CFG.N_SHIFTS, "flavours": 2,
+           "bytes": "2 n V field sites + FP32 links + FP64 force read and written"}
+    for name, prec in (("f32_fields", 1), ("f16_fields", 3)):
+        ms, b = force_probe(dims, prec, 2, CFG.N_SHIFTS, 20, quiet=True)
+        out[name] = {"us_per_launch": round(ms * 1e3, 2), "gb_per_launch": round(b / 1e9, 4),
+                     "gbs": round(b / ms / 1e6, 1), "frac_of_hbm": round(b / ms / 1e6 / peak, 4)}
     return out
 
 

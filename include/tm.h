@@ -213,6 +213,37 @@ tm_status tm_power_iteration(tm_ctx* ctx, tm_op op, int iters, double* lambda_ma
 tm_status tm_kernel_times(tm_ctx* ctx, tm_op op, tm_prec prec, const void* in, int reps, double* ms,
                           void* stream);
 
+/* Fermion-force outer products of the hopping term on every link (the force of
+ * the rational-approximation monomials, whose outer products of several
+ * two-flavour spinors Sec. 4.3 "Efficiency" reports as left on the CPU):
+ *
+ *   force_mu(x) += T_A[ U_mu(x) W_mu(x) ],
+ *   W_mu(x) = ph_mu(x) sum_k coeff[k] sum_flavour
+ *               [ X_k(x+mu) (x) ((1 - g_mu) Y_k(x))^*  +  ((1 + g_mu) Y_k(x+mu)) (x) X_k(x)^* ],
+ *
+ * with (a (x) b^*)_ij = a_i conj(b_j) over colour (spin summed), ph_mu(x) = bc_t
+ * of the last tm_clover_compute on the time links crossing t = T-1 -> 0 (1
+ * elsewhere), and T_A[Z] = (Z - Z^+)/2 - tr(Z - Z^+)/6 the traceless
+ * anti-hermitian part.  force_mu(x) is then the derivative of
+ * S = sum_k coeff[k] Re <Y_k, H X_k> along U_mu(x) -> exp(t w) U_mu(x), w in su(3):
+ * dS/dt = Re tr(w force_mu(x)).  The clover term's own link dependence is not
+ * included.
+ *   prec      storage precision of the fields: TM_F32, TM_BF16 or TM_F16 (the
+ *             products are formed in FP32; TM_F64 fields are rejected)
+ *   nflavour  1 or 2
+ *   n         field pairs, 0 <= n <= TM_FORCE_MAXN (n = 0: nothing to do)
+ *   coeff     host array of n weights
+ *   x, y      host arrays of 2n device pointers: x[2k + p] is the native field
+ *             X_k (tm_field_bytes of prec, nflavour) on the sites of parity p
+ *             (p = 0 even, 1 odd; tm_field_import converts either parity's
+ *             canonical half-lattice array, site k having lex/2 == k), 16-byte aligned
+ *   force     device, canonical FP64 gauge layout [t][z][y][x][mu][3][3] (re, im),
+ *             16-byte aligned; accumulated into
+ * Needs a loaded gauge field (TM_ERR_STALE otherwise).  Stream-ordered, one launch. */
+#define TM_FORCE_MAXN 32
+tm_status tm_force_outer(tm_ctx* ctx, tm_prec prec, int nflavour, int n, const double* coeff,
+                         const void* const* x, const void* const* y, double* force, void* stream);
+
 /* ---------------------------------------------------------------------------
  * Learned preconditioner: gauge-equivariant parallel-transport network (PTC).
  * Not in the paper, which preconditions its hardest solves by multigrid

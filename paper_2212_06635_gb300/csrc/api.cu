@@ -14,6 +14,7 @@
 #include <numeric>
 #include <vector>
 
+#include "force.h"
 #include "tm_host.h"
 #include "ptc.h"
 
@@ -603,6 +604,47 @@ extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const vo
     if (nf == 2 && !c->have_heavy) return fail(TM_ERR_ARG, "tm_kernel_times: no heavy clover term");
     return kernel_times_any(c, prec, nf, sign, in, reps, ms, st, c->variant[prec][nf - 1][0],
                             c->variant[prec][nf - 1][1]);
+}
+
+// ---------------------------------------------------------------------------
+// force outer products of the hopping term (Sec. 4.3, rational-approximation force)
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_force_outer(tm_ctx* c, tm_prec prec, int nf, int n, const double* coeff,
+                                    const void* const* x, const void* const* y, double* force, void* stream) {
+    if (!c || !force) return fail(TM_ERR_ARG, "tm_force_outer: bad pointers");
+    if (nf != 1 && nf != 2) return fail(TM_ERR_ARG, "tm_force_outer: nflavour must be 1 or 2");
+    if (n < 0 || n > FORCE_MAXN) return fail(TM_ERR_ARG, "tm_force_outer: n = %d outside [0, %d]", n, FORCE_MAXN);
+    if (prec != TM_F32 && prec != TM_BF16 && prec != TM_F16)
+        return fail(TM_ERR_ARG, "tm_force_outer: fields must be TM_F32, TM_BF16 or TM_F16");
+    if ((uintptr_t)force & 15) return fail(TM_ERR_ARG, "tm_force_outer: force must be 16-byte aligned");
+    if (n > 0 && (!coeff || !x || !y)) return fail(TM_ERR_ARG, "tm_force_outer: bad pointers");
+    CK(cudaSetDevice(c->device));
+    if (!is_device_ptr(force)) return fail(TM_ERR_ARG, "tm_force_outer: force must be a device pointer");
+    ForceArgs a{};
+    a.g = c->g;
+    a.n = n;
+    for (int k = 0; k < n; ++k) {
+        for (int p = 0; p < 2; ++p) {
+            const void* xp = x[2 * k + p];
+            const void* yp = y[2 * k + p];
+            if (!xp || !yp || (((uintptr_t)xp | (uintptr_t)yp) & 15))
+                return fail(TM_ERR_ARG, "tm_force_outer: field pair %d parity %d: null or misaligned", k, p);
+            if (!is_device_ptr(xp) || !is_device_ptr(yp))
+                return fail(TM_ERR_ARG, "tm_force_outer: field pair %d parity %d: not a device pointer", k, p);
+            a.x[k][p] = xp;
+            a.y[k][p] = yp;
+        }
+        a.c[k] = (float)coeff[k];
+    }
+    const cudaStream_t st = S(stream);
+    CKS(ensure_prec(c, P32, st));   // FP32 links (and the boundary phase of tm_clover_compute)
+    if (n == 0) return TM_OK;
+    a.bc_t = (float)c->params.bc_t;
+    a.gauge[0] = c->gaugeP[P32][0];
+    a.gauge[1] = c->gaugeP[P32][1];
+    a.force = force;
+    CK(launch_force_outer(prec, nf, a, st));
+    return TM_OK;
 }
 
 // ---------------------------------------------------------------------------

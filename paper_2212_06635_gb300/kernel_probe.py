@@ -106,6 +106,58 @@ def ptc_probe(dims, reps):
         tm.tm_destroy(ctx)
 
 
+def force_bytes(dims, prec, nf, n):
+    """Algorithmic bytes of one tm_force_outer launch: every field read once
+    (2 n fields on V sites), the FP32 links once (12 reals per link), the FP64
+    force read and written once."""
+    V = int(np.prod(dims))
+    site = nf * 24 * ESZ[prec] + (4 if prec >= 2 else 0)
+    return 2 * n * V * site + V * 4 * 12 * 4 + 2 * V * 4 * 18 * 8
+
+
+def force_probe(dims, prec, nf, n, reps, quiet=False):
+    """Time tm_force_outer on n distinct (X_k, Y_k) pairs of native fields of both
+    parities (seeded values, imported once and copied on the device), 1 + reps
+    launches, CUDA events around the last reps.  Returns (ms per launch, bytes)."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    u = F.gauge_field(dims, 1002)
+    ctx = tm.tm_create(dims, 0)
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, 0.14, 1.69, mu=0.0015)
+        nbytes = tm.tm_field_bytes(ctx, prec, nf)
+        seeds = []
+        for s in range(4):
+            src = torch.from_numpy(F.odd_spinor(dims, 2100 + s, nf).view(np.float64).copy()).cuda()
+            f = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+            tm.tm_field_import(ctx, prec, nf, f, src)
+            seeds.append(f)
+            del src
+        fields = [[seeds[(2 * w + p) % 4].clone() for p in range(2)] for w in range(2 * n)]
+        xs, ys = fields[:n], fields[n:]
+        c = [1.0 / (1 + k) for k in range(n)]
+        force = torch.zeros(int(np.prod(dims)) * 4 * 18, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        tm.tm_force_outer(ctx, prec, nf, c, xs, ys, force)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            tm.tm_force_outer(ctx, prec, nf, c, xs, ys, force)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / max(reps, 1)
+        b = force_bytes(dims, prec, nf, n)
+        if not quiet:
+            print(f"dims {dims} force outer products: {n} pairs, nf {nf}, fields {[k for k, v in PRECS.items() if v == prec][0]}: "
+                  f"{ms * 1e3:.1f} us per launch, {b / ms / 1e6:.0f} GB/s algorithmic ({b / 1e9:.3f} GB)")
+        return ms, b
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
@@ -121,6 +173,9 @@ def main():
                     help="instead: ITERS iterations of flexible CG with an untrained 1-8-8-8-1 network")
     ap.add_argument("--ptc-grad", action="store_true",
                     help="instead: loss and gradient of a 1-8-8-8-1 PTC network on one pair, (1 + reps) times")
+    ap.add_argument("--force", type=int, default=0, metavar="NPAIRS",
+                    help="instead: the force outer products of NPAIRS field pairs (--heavy: two flavours, "
+                         "--prec: field storage f32 / f16 / bf16), (1 + reps) launches")
     a = ap.parse_args()
     import torch
     from paper_2212_06635_gb300 import tm
@@ -132,6 +187,8 @@ def main():
         return ptc_grad_probe(dims, a.reps)
     if a.ptc_fcg:
         return ptc_fcg_probe(dims, a.ptc_fcg)
+    if a.force:
+        return force_probe(dims, PRECS[a.prec], 2 if a.heavy else 1, a.force, a.reps)
     prec = PRECS[a.prec]
     nf = 2 if a.heavy else 1
     u = F.gauge_field(dims, 1001)

@@ -82,6 +82,8 @@ _sigs = {
                        ct.POINTER(_vp), ct.POINTER(tm_solve_info), _vp],
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
+    "tm_force_outer": [_vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(_vp),
+                       ct.POINTER(_vp), _vp, _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_field_norm2_noalloc": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_ptc_create": [ct.POINTER(_vp), ct.c_int, ct.POINTER(ct.c_int), ct.c_int],
@@ -255,6 +257,24 @@ def tm_kernel_times(ctx, op, prec, inp, reps=20, stream=None):
     ms = (ct.c_double * 2)()
     _check(lib.tm_kernel_times(ctx, int(op), int(prec), ptr(inp), int(reps), ms, _stream(stream)))
     return ms[0], ms[1]
+
+
+TM_FORCE_MAXN = 32
+
+
+def tm_force_outer(ctx, prec, nflavour, coeffs, xs, ys, force, stream=None, check=True):
+    """force += T_A[U W] on every link for the field pairs (X_k, Y_k) with weights
+    coeffs[k]; xs[k], ys[k] = (even-parity native field, odd-parity native field)."""
+    n = len(coeffs)
+    if len(xs) != n or len(ys) != n:
+        raise ValueError("one (even, odd) field pair of X and of Y per weight")
+    cf = (ct.c_double * max(n, 1))(*coeffs)
+    xp = (_vp * max(2 * n, 1))(*[ptr(f) for pair in xs for f in pair])
+    yp = (_vp * max(2 * n, 1))(*[ptr(f) for pair in ys for f in pair])
+    st = lib.tm_force_outer(ctx, int(prec), int(nflavour), n, cf, xp, yp, ptr(force), _stream(stream))
+    if check:
+        _check(st)
+    return st
 
 
 def tm_autotune(ctx, prec, nflavour=1, stream=None):

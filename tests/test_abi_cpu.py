@@ -44,3 +44,11 @@ def test_null_arguments_rejected(tm):
     assert tm.lib.tm_destroy(None) == tm.TM_OK
     v = ct.c_double()
     assert tm.lib.tm_gauge_id(None, ct.byref(v)) == tm.TM_ERR_ARG
+
+
+def test_force_outer_host_checks(tm):
+    """Argument checks of tm_force_outer that run before any CUDA call."""
+    assert tm.lib.tm_force_outer(None, 1, 2, 0, None, None, None, None, None) == tm.TM_ERR_ARG
+    assert "bad pointers" in tm.tm_last_error()
+    with pytest.raises(ValueError):
+        tm.tm_force_outer(None, 1, 2, [1.0, 2.0], [(0, 0)], [(0, 0)], 0)
