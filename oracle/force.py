@@ -102,3 +102,31 @@ def action(geo: D.Geometry, U, X, Y, coeffs, bc_t=-1.0):
         hx = D.hop(geo, U, X[k], bc_t)
         s += c * float(np.real(np.vdot(Y[k], hx)))
     return s
+
+
+def schur_pairs(op: D.TwistedMassClover, a_o, b_o, sign=+1, heavy=False):
+    """Full-lattice fields (X, Y) whose hopping force, with weight -kappa^2, is the
+    derivative of Re <a, Q_hat_sign b> along the links with the clover term held
+    fixed (Q_hat of eq:hQpm, or of eq:hQh when heavy).
+
+    Q_hat = g5 [M_oo - kappa^2 H_oe M_ee^-1 H_eo], so varying the two hops gives
+        Re <g5 a, dH_oe R_s b> + Re <(M_ee^-1)^+ H_oe^+ g5 a, dH_eo b>,  R_s = M_ee(s)^-1 H_eo,
+    with (M_ee(s)^-1)^+ = M_ee(-s)^-1 (the twist flips sign), H^+ = g5 H g5 and g5
+    commuting with M_ee, so the second even field is g5 R_-s a.  The two pairs
+    live on opposite parities, so one pair carries both:
+        X = (R_s b on even sites, b on odd sites),  Y = g5 (R_-s a, a).
+    """
+    geo = op.geo
+
+    def R(psi_o, s):
+        h_e = D.hop(geo, op.U, geo.embed_odd(psi_o), op.bc_t, geo.even)
+        inv = op.inv_even_heavy(s) if heavy else op.inv_even_light(s)
+        return D.apply_local(inv, h_e)
+
+    X = np.zeros((geo.V,) + b_o.shape[1:], dtype=np.complex128)
+    Y = np.zeros_like(X)
+    X[geo.even] = R(b_o, sign)
+    X[geo.odd] = b_o
+    Y[geo.even] = D.g5(R(a_o, -sign))
+    Y[geo.odd] = D.g5(a_o)
+    return X, Y

@@ -108,3 +108,34 @@ def test_force_algebra_and_sites():
     assert np.max(np.abs(F1 + F2 - Fo)) < 1e-12
     s = np.array([0, 17, 100, geo.V - 1])
     assert np.max(np.abs(FO.hop_force(geo, U, X, Y, c, sites=s) - Fo[s])) < 1e-13
+
+
+@pytest.mark.parametrize("heavy,sign", [(False, +1), (False, -1), (True, +1), (True, -1)])
+def test_schur_hopping_force(heavy, sign):
+    """The pair built by schur_pairs gives, with weight -kappa^2, the derivative of
+    Re <a, Q_hat_sign b> along su(3) directions of every link, the clover term
+    held at its value for the unperturbed links (its own link dependence is not
+    part of the hopping force)."""
+    dims = (4, 4, 2, 4)
+    kappa, csw = 0.1394, 1.69
+    u = F.gauge_field(dims, 1501)
+    kw = dict(mubar=0.1246, epsbar=0.135) if heavy else dict(mu=0.01)
+    op = D.TwistedMassClover(u, dims, kappa, csw, **kw)
+    nf = 2 if heavy else 1
+    a = F.odd_spinor(dims, 1502, nf)
+    b = F.odd_spinor(dims, 1503, nf)
+    X, Y = FO.schur_pairs(op, a, b, sign, heavy)
+    Fo = FO.hop_force(op.geo, op.U, X[None], Y[None], [-kappa ** 2], op.bc_t)
+    omega = _random_su3_algebra((op.geo.V, 4), 1504)
+    pred = float(np.real(np.einsum("nmab,nmba->", omega, Fo)))
+
+    def form(t):
+        ut = np.einsum("nmab,nmbc->nmac", _expm_anti(t * omega), op.U).reshape(u.shape)
+        opt = D.TwistedMassClover(ut, dims, kappa, csw, **kw)
+        opt._A = op.A                      # clover held fixed
+        q = opt.Qhat_heavy(b, sign) if heavy else opt.Qhat(b, sign)
+        return float(np.real(np.vdot(a, q)))
+
+    h = 1e-4
+    fd = (form(h) - form(-h)) / (2 * h)
+    assert abs(pred - fd) <= 1e-7 * max(1.0, abs(fd)), (pred, fd)
