@@ -180,6 +180,14 @@ tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, 
 tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,
                         void* stream);
 
+/* The even pass of one Schur operator alone: out = M_ee(s)^-1 H_eo in, the even
+ * sites' reconstruction term of eq:hQpm / eq:hQh (x_e = M_ee^-1 (b_e + kappa H_eo x_o)
+ * for the full system).  op = TM_QHAT_PLUS / TM_QH (s = +) or TM_QHAT_MINUS /
+ * TM_QH_DAG (s = -); in: native odd-site field, out: native field of the same
+ * precision and flavour count holding the even sites (site k has lex/2 == k).
+ * Stream-ordered; the errors of tm_apply_Mhat. */
+tm_status tm_apply_even(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in, void* stream);
+
 /* Solve A x = b, A = TM_MDAGM, TM_QPQM, TM_QH_SQ or TM_WHAT_SQ, by CG (sloppy = TM_F64) or by
  * mixed-precision CG with reliable updates (Sec. 4.1).  x, b canonical FP64, host
  * or device pointers; x is the initial guess on entry (zero it for none). */
@@ -237,12 +245,24 @@ tm_status tm_kernel_times(tm_ctx* ctx, tm_op op, tm_prec prec, const void* in, i
  *             X_k (tm_field_bytes of prec, nflavour) on the sites of parity p
  *             (p = 0 even, 1 odd; tm_field_import converts either parity's
  *             canonical half-lattice array, site k having lex/2 == k), 16-byte aligned
+ *   gamma5_y  non-zero: every Y_k enters as g5 Y_k
  *   force     device, canonical FP64 gauge layout [t][z][y][x][mu][3][3] (re, im),
  *             16-byte aligned; accumulated into
- * Needs a loaded gauge field (TM_ERR_STALE otherwise).  Stream-ordered, one launch. */
+ * Needs a loaded gauge field and a current clover term (TM_ERR_STALE otherwise).
+ * Stream-ordered, one launch.
+ *
+ * Schur operators.  For odd fields a, b, the derivative of Re <a, Q_hat_s b>
+ * through the two hops of Q_hat_s = g5 [M_oo - kappa^2 H_oe M_ee(s)^-1 H_eo]
+ * (clover term held fixed) is the force of the single pair
+ *   X = (R_s b on even sites, b on odd sites),  Y = (R_-s a, a),  gamma5_y = 1,
+ * with weight -kappa^2, where R_s = M_ee(s)^-1 H_eo comes from tm_apply_even
+ * (s = + for TM_QHAT_PLUS / TM_QH, - for TM_QHAT_MINUS / TM_QH_DAG).  For a
+ * rational force, pass one such pair per shift, weighted by -kappa^2 times the
+ * shift's coefficient. */
 #define TM_FORCE_MAXN 32
 tm_status tm_force_outer(tm_ctx* ctx, tm_prec prec, int nflavour, int n, const double* coeff,
-                         const void* const* x, const void* const* y, double* force, void* stream);
+                         const void* const* x, const void* const* y, int gamma5_y, double* force,
+                         void* stream);
 
 /* ---------------------------------------------------------------------------
  * Learned preconditioner: gauge-equivariant parallel-transport network (PTC).

@@ -458,6 +458,41 @@ extern "C" tm_status tm_apply_Mhat(tm_ctx* c, tm_op op, tm_prec prec, void* out,
     return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown precision");
 }
 
+// the even pass alone: out (even sites) = M_ee(sign)^-1 H_eo in (odd sites)
+template <int P, int NF>
+static cudaError_t even_t(const tm_ctx* c, int sign, void* out, const void* in, cudaStream_t st) {
+    OpBatch<1> b{};
+    b.n = 1;
+    b.fin = FIN_NONE;
+    b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, out, in, nullptr, nullptr, false);
+    b.blk_start[0] = 0;
+    b.blk_start[1] = b.p[0].nblk;
+    return launch_pass<P, NF, K1_EO_INV, 1>(c->variant[P][NF - 1][K1_EO_INV], b, b.p[0].nblk, st);
+}
+
+extern "C" tm_status tm_apply_even(tm_ctx* c, tm_op op, tm_prec prec, void* out, const void* in, void* stream) {
+    if (!c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_apply_even: bad pointers");
+    if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_even: fields must be 16-byte aligned");
+    if (op != TM_QHAT_PLUS && op != TM_QHAT_MINUS && op != TM_QH && op != TM_QH_DAG)
+        return fail(TM_ERR_ARG, "tm_apply_even: op must be a single Schur operator");
+    CKS(check_prec(prec));
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ensure_prec(c, prec, st));
+    const int nf = nflav(op);
+    if (nf == 2 && !c->have_heavy)
+        return fail(TM_ERR_ARG, "tm_apply_even: heavy operator needs mubar or epsbar in tm_clover_compute");
+    const int sign = (op == TM_QHAT_PLUS || op == TM_QH) ? +1 : -1;
+    const bool h = nf == 2;
+    switch (prec) {
+        case TM_F64: CK(h ? even_t<P64, 2>(c, sign, out, in, st) : even_t<P64, 1>(c, sign, out, in, st)); break;
+        case TM_F32: CK(h ? even_t<P32, 2>(c, sign, out, in, st) : even_t<P32, 1>(c, sign, out, in, st)); break;
+        case TM_BF16: CK(h ? even_t<PB16, 2>(c, sign, out, in, st) : even_t<PB16, 1>(c, sign, out, in, st)); break;
+        case TM_F16: CK(h ? even_t<PF16, 2>(c, sign, out, in, st) : even_t<PF16, 1>(c, sign, out, in, st)); break;
+    }
+    return TM_OK;
+}
+
 // ---------------------------------------------------------------------------
 // fields
 // ---------------------------------------------------------------------------
@@ -610,7 +645,8 @@ extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const vo
 // force outer products of the hopping term (Sec. 4.3, rational-approximation force)
 // ---------------------------------------------------------------------------
 extern "C" tm_status tm_force_outer(tm_ctx* c, tm_prec prec, int nf, int n, const double* coeff,
-                                    const void* const* x, const void* const* y, double* force, void* stream) {
+                                    const void* const* x, const void* const* y, int gamma5_y, double* force,
+                                    void* stream) {
     if (!c || !force) return fail(TM_ERR_ARG, "tm_force_outer: bad pointers");
     if (nf != 1 && nf != 2) return fail(TM_ERR_ARG, "tm_force_outer: nflavour must be 1 or 2");
     if (n < 0 || n > FORCE_MAXN) return fail(TM_ERR_ARG, "tm_force_outer: n = %d outside [0, %d]", n, FORCE_MAXN);
@@ -643,6 +679,7 @@ extern "C" tm_status tm_force_outer(tm_ctx* c, tm_prec prec, int nf, int n, cons
     a.gauge[0] = c->gaugeP[P32][0];
     a.gauge[1] = c->gaugeP[P32][1];
     a.force = force;
+    a.g5y = gamma5_y ? 1 : 0;
     CK(launch_force_outer(prec, nf, a, st));
     return TM_OK;
 }

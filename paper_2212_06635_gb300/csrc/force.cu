@@ -10,6 +10,8 @@
 //                                            + ((1 + g_mu) Y_k(x+mu)) (x) X_k(x)^* ]
 //   force_mu(x) += T_A[ U_mu(x) W_mu(x) ]    (traceless anti-hermitian part)
 //
+// (optionally with g5 Y_k in place of Y_k, the form the Schur operators' force
+// takes)
 // so that force_mu(x) is the derivative of S = sum_k c_k Re <Y_k, H[U] X_k>
 // along su(3) directions of U_mu(x) (H the hopping term).
 //
@@ -89,8 +91,12 @@ __device__ __forceinline__ void force_outer2(cpx<float> (&w)[9], const cpx<float
         }
 }
 
-template <int P, int NF, int MU>
+// G5: the Y fields enter as g5 Y.  P_s(g5 B) = B_up - s G B_down = P_-s(B), so
+// g5 only flips the projection sign of the Y spinors.
+template <int P, int NF, int MU, bool G5>
 __device__ __forceinline__ void force_link(const ForceArgs& a, long i, int par, const Coord& c) {
+    constexpr int SY1 = G5 ? +1 : -1;   // sign of Y(x) in the forward term
+    constexpr int SY2 = G5 ? -1 : +1;   // sign of Y(x+mu) in the backward term
     const Geom& g = a.g;
     int xf = c.x, yf = c.y, zf = c.z, tf = c.t;
     float ph = 1.f;
@@ -121,12 +127,12 @@ __device__ __forceinline__ void force_link(const ForceArgs& a, long i, int par, 
             force_load<P, NF>(xn, vh, j, f, p, s1);
             force_load<P, NF>(ys, vh, i, f, q, s2);
             force_half<MU, -1>(hu, p, 1.f);
-            force_half<MU, -1>(hv, q, ck * s1 * s2);
+            force_half<MU, SY1>(hv, q, ck * s1 * s2);
             force_outer2(w, hu, hv);
             // backward hop at x+mu (through U_mu(x)^dagger): ((1 + g_mu) Y(x+mu)) (x) X(x)^*
             force_load<P, NF>(yn, vh, j, f, p, s1);
             force_load<P, NF>(xs, vh, i, f, q, s2);
-            force_half<MU, +1>(hu, p, 1.f);
+            force_half<MU, SY2>(hu, p, 1.f);
             force_half<MU, +1>(hv, q, ck * s1 * s2);
             force_outer2(w, hu, hv);
         }
@@ -163,7 +169,7 @@ __device__ __forceinline__ void force_link(const ForceArgs& a, long i, int par, 
         }
 }
 
-template <int P, int NF>
+template <int P, int NF, bool G5>
 __global__ void __launch_bounds__(256) force_outer_kernel(const __grid_constant__ ForceArgs a) {
     const long i = (long)blockIdx.x * 32 + threadIdx.x;
     if (i >= a.g.vh) return;
@@ -171,17 +177,20 @@ __global__ void __launch_bounds__(256) force_outer_kernel(const __grid_constant_
     const int par = threadIdx.z;
     const Coord c = cb_coords(a.g, i, par);
     switch (mu) {   // warp-uniform
-        case 0: force_link<P, NF, 0>(a, i, par, c); break;
-        case 1: force_link<P, NF, 1>(a, i, par, c); break;
-        case 2: force_link<P, NF, 2>(a, i, par, c); break;
-        default: force_link<P, NF, 3>(a, i, par, c); break;
+        case 0: force_link<P, NF, 0, G5>(a, i, par, c); break;
+        case 1: force_link<P, NF, 1, G5>(a, i, par, c); break;
+        case 2: force_link<P, NF, 2, G5>(a, i, par, c); break;
+        default: force_link<P, NF, 3, G5>(a, i, par, c); break;
     }
 }
 
 template <int P, int NF>
 static cudaError_t launch_t(const ForceArgs& a, cudaStream_t st) {
     const long nblk = (a.g.vh + 31) / 32;
-    force_outer_kernel<P, NF><<<(unsigned)nblk, dim3(32, 4, 2), 0, st>>>(a);
+    if (a.g5y)
+        force_outer_kernel<P, NF, true><<<(unsigned)nblk, dim3(32, 4, 2), 0, st>>>(a);
+    else
+        force_outer_kernel<P, NF, false><<<(unsigned)nblk, dim3(32, 4, 2), 0, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -15,6 +15,7 @@ struct ForceArgs {
     const void* x[FORCE_MAXN][2];   // native fields X_k of parity 0 / 1
     const void* y[FORCE_MAXN][2];   // native fields Y_k of parity 0 / 1
     float c[FORCE_MAXN];         // weights c_k
+    int g5y;                     // 1: the Y fields enter as g5 Y_k
     double* force;               // canonical FP64 [lex][mu][3][3] complex, accumulated
 };
 

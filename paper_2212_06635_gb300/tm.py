@@ -83,7 +83,8 @@ _sigs = {
     "tm_power_iteration": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_kernel_times": [_vp, ct.c_int, ct.c_int, _vp, ct.c_int, ct.POINTER(ct.c_double), _vp],
     "tm_force_outer": [_vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(_vp),
-                       ct.POINTER(_vp), _vp, _vp],
+                       ct.POINTER(_vp), ct.c_int, _vp, _vp],
+    "tm_apply_even": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_field_norm2_noalloc": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_ptc_create": [ct.POINTER(_vp), ct.c_int, ct.POINTER(ct.c_int), ct.c_int],
@@ -210,6 +211,11 @@ def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
     _check(lib.tm_apply_Mhat(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
 
 
+def tm_apply_even(ctx, op, prec, out, inp, stream=None):
+    """out (even sites) = M_ee(s)^-1 H_eo inp (odd sites), s the sign of op."""
+    _check(lib.tm_apply_even(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
+
+
 def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.0, chunk=16, use_graph=1, refine=TM_F64):
     """refine: multishift refinement storage precision (TM_F64 = same as sloppy);
     delta <= 0: the library's reliable-update threshold for the sloppy precision."""
@@ -262,16 +268,18 @@ def tm_kernel_times(ctx, op, prec, inp, reps=20, stream=None):
 TM_FORCE_MAXN = 32
 
 
-def tm_force_outer(ctx, prec, nflavour, coeffs, xs, ys, force, stream=None, check=True):
+def tm_force_outer(ctx, prec, nflavour, coeffs, xs, ys, force, gamma5_y=False, stream=None, check=True):
     """force += T_A[U W] on every link for the field pairs (X_k, Y_k) with weights
-    coeffs[k]; xs[k], ys[k] = (even-parity native field, odd-parity native field)."""
+    coeffs[k]; xs[k], ys[k] = (even-parity native field, odd-parity native field);
+    gamma5_y: the Y fields enter as g5 Y_k."""
     n = len(coeffs)
     if len(xs) != n or len(ys) != n:
         raise ValueError("one (even, odd) field pair of X and of Y per weight")
     cf = (ct.c_double * max(n, 1))(*coeffs)
     xp = (_vp * max(2 * n, 1))(*[ptr(f) for pair in xs for f in pair])
     yp = (_vp * max(2 * n, 1))(*[ptr(f) for pair in ys for f in pair])
-    st = lib.tm_force_outer(ctx, int(prec), int(nflavour), n, cf, xp, yp, ptr(force), _stream(stream))
+    st = lib.tm_force_outer(ctx, int(prec), int(nflavour), n, cf, xp, yp, int(bool(gamma5_y)), ptr(force),
+                            _stream(stream))
     if check:
         _check(st)
     return st

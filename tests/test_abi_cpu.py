@@ -48,7 +48,7 @@ def test_null_arguments_rejected(tm):
 
 def test_force_outer_host_checks(tm):
     """Argument checks of tm_force_outer that run before any CUDA call."""
-    assert tm.lib.tm_force_outer(None, 1, 2, 0, None, None, None, None, None) == tm.TM_ERR_ARG
+    assert tm.lib.tm_force_outer(None, 1, 2, 0, None, None, None, 0, None, None) == tm.TM_ERR_ARG
     assert "bad pointers" in tm.tm_last_error()
     with pytest.raises(ValueError):
         tm.tm_force_outer(None, 1, 2, [1.0, 2.0], [(0, 0)], [(0, 0)], 0)

@@ -172,3 +172,75 @@ def test_force_outer_full_size_sampled():
         assert rel(got, ref) < FORCE_TOL[1], rel(got, ref)
     finally:
         lat.close()
+
+
+def _schur_codes(tm, heavy, sign):
+    if heavy:
+        return (tm.TM_QH, tm.TM_QH_DAG) if sign > 0 else (tm.TM_QH_DAG, tm.TM_QH)
+    return (tm.TM_QHAT_PLUS, tm.TM_QHAT_MINUS) if sign > 0 else (tm.TM_QHAT_MINUS, tm.TM_QHAT_PLUS)
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3], ids=["f64", "f32", "f16"])
+@pytest.mark.parametrize("heavy,sign", [(False, +1), (False, -1), (True, +1), (True, -1)])
+def test_apply_even_parity(prec, heavy, sign):
+    """tm_apply_even = M_ee(s)^-1 H_eo on the even sites (the even pass alone)."""
+    from tests.gpu_util import tol
+    dims = (6, 4, 4, 6)
+    u = F.gauge_field(dims, 1611)
+    kw = dict(mubar=0.1246, epsbar=0.135) if heavy else dict(mu=MU)
+    op = D.TwistedMassClover(u, dims, KAPPA, CSW, **kw)
+    lat = Lat(u, dims, KAPPA, CSW, **kw)
+    try:
+        tm = lat.tm
+        nf = 2 if heavy else 1
+        psi = F.odd_spinor(dims, 1612, nf)
+        src = to_dev(psi)
+        a = lat.native(prec, nf)
+        o = lat.native(prec, nf)
+        tm.tm_field_import(lat.ctx, prec, nf, a, src)
+        tm.tm_apply_even(lat.ctx, _schur_codes(tm, heavy, sign)[0], prec, o, a)
+        out = src.clone()
+        tm.tm_field_export(lat.ctx, prec, nf, out, o)
+        got = from_dev(out, psi.shape)
+        geo = op.geo
+        h_e = D.hop(geo, op.U, geo.embed_odd(psi), op.bc_t, geo.even)
+        inv = op.inv_even_heavy(sign) if heavy else op.inv_even_light(sign)
+        ref = D.apply_local(inv, h_e)
+        assert rel(got, ref) < tol(prec), rel(got, ref)
+    finally:
+        lat.close()
+
+
+@pytest.mark.parametrize("heavy,sign", [(False, +1), (False, -1), (True, +1), (True, -1)])
+def test_schur_force_through_the_library(heavy, sign):
+    """The hopping force of Re <a, Q_hat_s b> computed by the library alone: the
+    even reconstructions R_s b and R_-s a from tm_apply_even, then one
+    tm_force_outer pair with g5 on Y and weight -kappa^2, against the oracle's
+    pair (pinned by finite differences in test_oracle_force.py)."""
+    import torch
+    dims = (6, 4, 4, 6)
+    u = F.gauge_field(dims, 1601)
+    kw = dict(mubar=0.1246, epsbar=0.135) if heavy else dict(mu=MU)
+    op = D.TwistedMassClover(u, dims, KAPPA, CSW, **kw)
+    lat = Lat(u, dims, KAPPA, CSW, **kw)
+    try:
+        tm = lat.tm
+        nf = 2 if heavy else 1
+        prec = 1
+        a = F.odd_spinor(dims, 1602, nf)
+        b = F.odd_spinor(dims, 1603, nf)
+        na, nb, ra, rb = (lat.native(prec, nf) for _ in range(4))
+        tm.tm_field_import(lat.ctx, prec, nf, na, to_dev(a))
+        tm.tm_field_import(lat.ctx, prec, nf, nb, to_dev(b))
+        cs, cms = _schur_codes(tm, heavy, sign)
+        tm.tm_apply_even(lat.ctx, cs, prec, rb, nb)
+        tm.tm_apply_even(lat.ctx, cms, prec, ra, na)
+        fd = torch.zeros(op.geo.V * 4 * 18, dtype=torch.float64, device="cuda:0")
+        tm.tm_force_outer(lat.ctx, prec, nf, [-KAPPA ** 2], [(rb, nb)], [(ra, na)], fd, gamma5_y=True)
+        torch.cuda.synchronize()
+        got = from_dev(fd, (op.geo.V, 4, 3, 3))
+        X, Y = FO.schur_pairs(op, a, b, sign, heavy)
+        ref = FO.hop_force(op.geo, op.U, X[None], Y[None], [-KAPPA ** 2], op.bc_t)
+        assert rel(got, ref) < FORCE_TOL[1], rel(got, ref)
+    finally:
+        lat.close()
