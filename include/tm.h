@@ -204,7 +204,8 @@ tm_status tm_solve_multishift(tm_ctx* ctx, tm_op op, int nshift, const double* s
 
 /* n independent solves A_i x_i = b_i on contexts of possibly different volumes, all
  * advanced together by batched kernels (one launch per step covers every
- * problem).  n <= 32. */
+ * problem).  n <= 32.  The stencil variants are those chosen (tm_autotune /
+ * tm_set_tuning) for the context with the most sites. */
 tm_status tm_solve_batch(tm_ctx** ctxs, int n, tm_op op, const tm_solve_params* sp,
                          double** x, const double** b, tm_solve_info* infos, void* stream);
 

@@ -1374,8 +1374,13 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
     VecBatch<MAXP> pu{}, up{};
     int s1, s2;
     normal_signs(op, &s1, &s2);
-    // one kernel variant per pass for the whole batch (the first context's choice)
-    const int v1 = cs[0]->variant[PS][0][K1_EO_INV], v2 = cs[0]->variant[PS][0][K2_OE_LOCAL];
+    // one kernel variant per pass for the whole batch: the choice of the context
+    // with the most sites, whose problem dominates the batch's time (a small
+    // lattice's timing-based choice can differ and is noisy)
+    int qbig = 0;
+    for (int q = 1; q < n; ++q)
+        if (cs[q]->vh > cs[qbig]->vh) qbig = q;
+    const int v1 = cs[qbig]->variant[PS][0][K1_EO_INV], v2 = cs[qbig]->variant[PS][0][K2_OE_LOCAL];
     int ob1 = 0, ob2 = 0, vbk = 0;
     for (int q = 0; q < n; ++q) {
         tm_ctx* c = cs[q];
