@@ -17,4 +17,7 @@ Paper: "Twisted mass ensemble generation on GPU machines" (arXiv 2212.06635).
               (not in the paper; parity of its training trajectory unpinned)
   force.py    fermion-force outer products of the hopping term on every link
               (the rational-approximation force step of Sec. 4.3)
+  rational.py Zolotarev's rational approximation of A^-1/2, its application in
+              partial fractions, and the binomial series of the correction
+              term (Sec. 4.2, Fig. 4's heatbath and acceptance)
 """
