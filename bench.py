@@ -333,6 +333,7 @@ def run_ours(args, rank, world, local_rank):
         extra["multishift_heavy_24x48"] = run_multishift(tm, args)
         extra["batch_uneven_24"] = run_batch(tm, args)
         extra["force_outer_heavy_24x48"] = run_force(args, peak)
+        extra["rational_correction_heavy_24x48"] = run_rational(tm, args)
     if rank == 0 and not args.no_ptc:
         try:
             extra["ptc_fcg_48x96"] = run_ptc(tm, args)
@@ -474,6 +475,50 @@ def run_force(args, peak):
         ms, b = force_probe(dims, prec, 2, CFG.N_SHIFTS, 20, quiet=True)
         out[name] = {"us_per_launch": round(ms * 1e3, 2), "gb_per_launch": round(b / 1e9, 4),
                      "gbs": round(b / ms / 1e6, 1), "frac_of_hbm": round(b / ms / 1e6 / peak, 4)}
+    return out
+
+
+def run_rational(tm, args):
+    """The rational approximation's correction term on the heavy doublet at
+    24^3x48 (Fig. 4's table): Zolotarev r(x) ~ x^-1/2 with 12 poles on
+    [1e-5, 1] x 1.02 lambda_max; heatbath phi = (1 + Z)^-1/4 eta and acceptance
+    <phi, (1 + Z)^1/2 phi>, Z = A r(A)^2 - 1, each rational application one
+    multishift solve refined to 1e-10, for the three multishift forms."""
+    import torch
+    w = CFG.HEAVY_24
+    u = F.gauge_field(w.dims, w.link_seed)
+    eta = F.odd_spinor(w.dims, w.rhs_seed + 1, 2)
+    ctx = tm.tm_create(w.dims, 0)
+    out = {"workload": "heavy doublet 24^3x48 rational correction term", "poles": CFG.N_SHIFTS}
+    try:
+        tm.tm_gauge_load(ctx, u, 1.0)
+        tm.tm_clover_compute(ctx, w.kappa, w.csw, mubar=w.mubar, epsbar=w.epsbar, bc_t=w.bc_t)
+        for p in (tm.TM_F32, tm.TM_F16):
+            tm.tm_autotune(ctx, p, 2)
+        lmax = 1.02 * tm.tm_power_iteration(ctx, tm.TM_QH_SQ, 100)
+        coeffs = tm.tm_rational_inv_sqrt(CFG.N_SHIFTS, 1e-5 * lmax, lmax)
+        out["delta"] = coeffs[3]
+        ed = torch.from_numpy(eta.view(np.float64).copy()).cuda()
+        ee = float(torch.dot(ed, ed))
+        forms = (("double", tm.TM_F64, tm.TM_F64), ("single_single", tm.TM_F32, tm.TM_F64),
+                 ("single_half", tm.TM_F32, tm.TM_F16))
+        for name, sl, rf in forms:
+            sp = tm.solve_params(tol=w.tol, sloppy=sl, refine=rf)
+            phi = torch.zeros_like(ed)
+            acc = torch.zeros_like(ed)
+            _sync()
+            t0 = time.perf_counter()
+            _, n1 = tm.tm_rational_correction(ctx, tm.TM_QH_SQ, coeffs, -0.25, phi, ed, sp, series_tol=1e-10)
+            _sync()
+            t1 = time.perf_counter()
+            _, n2 = tm.tm_rational_correction(ctx, tm.TM_QH_SQ, coeffs, 0.5, acc, phi, sp, series_tol=1e-10)
+            energy = float(torch.dot(phi, acc))
+            _sync()
+            t2 = time.perf_counter()
+            out[name] = {"heatbath_s": round(t1 - t0, 4), "acceptance_s": round(t2 - t1, 4),
+                         "z_applications": [n1, n2], "energy_minus_eta2_rel": (energy - ee) / ee}
+    finally:
+        tm.tm_destroy(ctx)
     return out
 
 

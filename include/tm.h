@@ -202,6 +202,36 @@ tm_status tm_solve_multishift(tm_ctx* ctx, tm_op op, int nshift, const double* s
                               double** x, const double* b, const tm_solve_params* sp,
                               tm_solve_info* infos, void* stream);
 
+/* Rational approximation of x^-1/2 on [lo, hi] with n poles (1 <= n <= 16), the
+ * form Sec. 4.2's rational monomials of the heavy doublet apply with one
+ * multishift solve: r(x) = a0 + sum_k a[k] / (x + sigma[k]), Zolotarev's best
+ * approximation in the relative sense; *delta = max |sqrt(x) r(x) - 1| on
+ * [lo, hi].  Host computation only (no context, no device). */
+tm_status tm_rational_inv_sqrt(int n, double lo, double hi, double* a0, double* a, double* sigma,
+                               double* delta);
+
+/* y = r(A) b = a0 b + sum_k a[k] (A + sigma[k])^-1 b for A = TM_MDAGM, TM_QPQM or
+ * TM_QH_SQ: one tm_solve_multishift (sloppy multishift CG, shift-by-shift
+ * refinement to sp->tol, Sec. 4.2) and one FP64 combination on the device.
+ * y, b: canonical FP64 (host or device); infos: n records of the solves.
+ * Synchronises like the solvers. */
+tm_status tm_rational_apply(tm_ctx* ctx, tm_op op, int n, double a0, const double* a, const double* sigma,
+                            double* y, const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                            void* stream);
+
+/* The correction term of the rational approximation (Fig. 4's heatbath and
+ * acceptance): y = (1 + Z)^p b with Z = A r(A)^2 - 1, r the rational function of
+ * (a0, a, sigma), summed as the binomial series sum_j binom(p, j) Z^j b until a
+ * term's norm is below series_tol ||b|| (at most 40 terms).  Each Z costs two
+ * rational applications and one FP64 A.  p = -1/4 gives the heatbath field
+ * phi = (1 + Z)^-1/4 eta, p = 1/2 the acceptance factor ((1 + Z)^1/2 phi, whose
+ * inner product with phi is the correction's energy).  *napply = number of Z
+ * applications; infos: the records of the last multishift solve. */
+tm_status tm_rational_correction(tm_ctx* ctx, tm_op op, int n, double a0, const double* a,
+                                 const double* sigma, double p, double series_tol, double* y,
+                                 const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                                 int* napply, void* stream);
+
 /* n independent solves A_i x_i = b_i on contexts of possibly different volumes, all
  * advanced together by batched kernels (one launch per step covers every
  * problem).  n <= 32.  The stencil variants are those chosen (tm_autotune /

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "force.h"
+#include "rational.h"
 #include "tm_host.h"
 #include "ptc.h"
 
@@ -128,7 +129,7 @@ enum WsId {
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
     WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO, WS_TUNE,
     WS_FCG_Z,
-    WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300
+    WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300, WS_RAT = 400
 };
 
 // ---------------------------------------------------------------------------
@@ -1207,24 +1208,12 @@ static tm_status multishift_dispatch(tm_ctx* c, tm_op op, int ns, const double* 
     return fail(TM_ERR_ARG, "unknown sloppy precision");
 }
 
-extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const double* shifts, double** x,
-                                         const double* b, const tm_solve_params* sp, tm_solve_info* infos,
-                                         void* stream) {
-    const auto t0 = std::chrono::steady_clock::now();
-    if (!c || !shifts || !x || !b || !sp || !infos) return fail(TM_ERR_ARG, "tm_solve_multishift: null argument");
-    if (ns < 1 || ns > MAX_SHIFTS) return fail(TM_ERR_ARG, "tm_solve_multishift: 1 <= nshift <= %d", MAX_SHIFTS);
-    for (int k = 0; k < ns; ++k)
-        if (!(shifts[k] >= 0.0) || !x[k]) return fail(TM_ERR_ARG, "tm_solve_multishift: shifts must be >= 0");
-    if (op != TM_MDAGM && op != TM_QH_SQ && op != TM_QPQM) return fail(TM_ERR_ARG, "tm_solve_multishift: bad op");
-    CKS(check_prec(sp->sloppy));
-    CKS(check_prec(sp->refine));
-    CK(cudaSetDevice(c->device));
-    CKS(check_solver_op(c, op));
-    const cudaStream_t st = c->sstream;
-    CKS(enter_solver(c, stream));
-    CKS(ensure_prec(c, P64, st));
-    CKS(ensure_prec(c, sp->sloppy, st));
-    if (sp->refine != TM_F64) CKS(ensure_prec(c, sp->refine, st));
+// Multishift CG in the sloppy precision plus shift-by-shift refinement (Sec. 4.2)
+// on a native FP64 right-hand side b64 (not a WS_MS_X64 field); the refined
+// solutions stay in the native FP64 workspace fields, xk[k] for shifts[k]
+// (null when the multishift solve itself failed and shift k has no solution).
+static tm_status ms_core(tm_ctx* c, tm_op op, int ns, const double* shifts, void* b64, const tm_solve_params* sp,
+                         tm_solve_info* infos, cudaStream_t st, std::vector<void*>& xk) {
     const int nf = nflav(op);
     const size_t b64sz = spinor_bytes(P64, 12 * nf, c->vh);
     std::vector<int> order(ns);
@@ -1232,33 +1221,216 @@ extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const doub
     std::stable_sort(order.begin(), order.end(), [&](int a, int bq) { return shifts[a] < shifts[bq]; });
     std::vector<double> sh(ns);
     for (int k = 0; k < ns; ++k) sh[k] = shifts[order[k]];
-    void* b64;
-    CKS(ws_get(c, WS_B64, b64sz, &b64));
-    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
     std::vector<void*> xk64(ns);
     for (int k = 0; k < ns; ++k) CKS(ws_get(c, WS_MS_X64 + k, b64sz, &xk64[k]));
     int ms_iters = 0;
     tm_status s = nf == 1 ? multishift_dispatch<1>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st)
                           : multishift_dispatch<2>(c, op, ns, sh.data(), b64, sp, xk64, &ms_iters, st);
     tm_status worst = s;
-    // shift-by-shift refinement with mixed-precision CG (Sec. 4.2), in its own
-    // storage precision when sp->refine names one
+    // shift-by-shift refinement with mixed-precision CG, in its own storage
+    // precision when sp->refine names one
     tm_solve_params rsp = *sp;
     if (sp->refine != TM_F64) rsp.sloppy = sp->refine;
+    xk.assign(ns, nullptr);
     for (int k = 0; k < ns; ++k) {
         tm_solve_info& inf = infos[order[k]];
         std::memset(&inf, 0, sizeof(inf));
         if (s != TM_OK) { inf.status = s; continue; }
+        xk[order[k]] = xk64[k];
         tm_status r = nf == 1 ? solve_dispatch<1>(c, op, sh[k], &rsp, xk64[k], b64, &inf, st)
                               : solve_dispatch<2>(c, op, sh[k], &rsp, xk64[k], b64, &inf, st);
         inf.iters += ms_iters;
         if (r != TM_OK && worst == TM_OK) worst = r;
-        CKS(stage_out(c, nf, x[order[k]], WS_STAGE_X, xk64[k], st));
+    }
+    return worst;
+}
+
+static tm_status ms_check(tm_ctx* c, tm_op op, int ns, const double* shifts, const tm_solve_params* sp,
+                          const char* who) {
+    if (ns < 1 || ns > MAX_SHIFTS) return fail(TM_ERR_ARG, "%s: 1 <= nshift <= %d", who, MAX_SHIFTS);
+    for (int k = 0; k < ns; ++k)
+        if (!(shifts[k] >= 0.0)) return fail(TM_ERR_ARG, "%s: shifts must be >= 0", who);
+    if (op != TM_MDAGM && op != TM_QH_SQ && op != TM_QPQM) return fail(TM_ERR_ARG, "%s: bad op", who);
+    CKS(check_prec(sp->sloppy));
+    CKS(check_prec(sp->refine));
+    CK(cudaSetDevice(c->device));
+    return check_solver_op(c, op);
+}
+
+static tm_status ms_prepare(tm_ctx* c, const tm_solve_params* sp, cudaStream_t st) {
+    CKS(ensure_prec(c, P64, st));
+    CKS(ensure_prec(c, sp->sloppy, st));
+    if (sp->refine != TM_F64) CKS(ensure_prec(c, sp->refine, st));
+    return TM_OK;
+}
+
+extern "C" tm_status tm_solve_multishift(tm_ctx* c, tm_op op, int ns, const double* shifts, double** x,
+                                         const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                                         void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    if (!c || !shifts || !x || !b || !sp || !infos) return fail(TM_ERR_ARG, "tm_solve_multishift: null argument");
+    CKS(ms_check(c, op, ns, shifts, sp, "tm_solve_multishift"));
+    for (int k = 0; k < ns; ++k)
+        if (!x[k]) return fail(TM_ERR_ARG, "tm_solve_multishift: null solution buffer");
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ms_prepare(c, sp, st));
+    const int nf = nflav(op);
+    void* b64;
+    CKS(ws_get(c, WS_B64, spinor_bytes(P64, 12 * nf, c->vh), &b64));
+    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
+    std::vector<void*> xk;
+    tm_status worst = ms_core(c, op, ns, shifts, b64, sp, infos, st, xk);
+    for (int k = 0; k < ns; ++k) {
+        if (!xk[k]) continue;
+        CKS(stage_out(c, nf, x[k], WS_STAGE_X, xk[k], st));
         CK(cudaStreamSynchronize(st));
     }
     CK(cudaStreamSynchronize(st));
     const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
     for (int k = 0; k < ns; ++k) infos[k].seconds = secs;
+    return worst;
+}
+
+// ---------------------------------------------------------------------------
+// rational approximation of A^-1/2 (Sec. 4.2's rational monomials and their
+// correction term, Fig. 4)
+// ---------------------------------------------------------------------------
+extern "C" tm_status tm_rational_inv_sqrt(int n, double lo, double hi, double* a0, double* a, double* sigma,
+                                          double* delta) {
+    if (!a0 || !a || !sigma || !delta || n < 1 || n > MAX_SHIFTS || !(lo > 0.0) || !(hi > lo))
+        return fail(TM_ERR_ARG, "tm_rational_inv_sqrt: need 1 <= n <= %d, 0 < lo < hi", MAX_SHIFTS);
+    if (!zolotarev_inv_sqrt(n, lo, hi, a0, a, sigma, delta)) return fail(TM_ERR_ARG, "tm_rational_inv_sqrt: failed");
+    return TM_OK;
+}
+
+// y64 = a0 b64 + sum_k a_k (A + sigma_k)^-1 b64, native FP64 fields (y64 may be b64)
+static tm_status rational_native(tm_ctx* c, tm_op op, int n, double a0, const double* a, const double* sigma,
+                                 void* y64, void* b64, const tm_solve_params* sp, tm_solve_info* infos,
+                                 cudaStream_t st, tm_status* worst) {
+    std::vector<void*> xk;
+    tm_status s = ms_core(c, op, n, sigma, b64, sp, infos, st, xk);
+    if (s != TM_OK && *worst == TM_OK) *worst = s;
+    for (int k = 0; k < n; ++k)
+        if (!xk[k]) return fail(s, "rational approximation: the multishift solve failed");
+    LinComb lc{};
+    lc.n = n;
+    lc.len = (long)c->vh * 12 * nflav(op);
+    lc.a0 = a0;
+    lc.b = reinterpret_cast<const double2*>(b64);
+    for (int k = 0; k < n; ++k) {
+        lc.x[k] = reinterpret_cast<const double2*>(xk[k]);
+        lc.a[k] = a[k];
+    }
+    lc.y = reinterpret_cast<double2*>(y64);
+    CK(launch_lincomb64(lc, st));
+    return TM_OK;
+}
+
+static tm_status rational_args(tm_ctx* c, tm_op op, int n, const double* a, const double* sigma, void* y,
+                               const void* b, const tm_solve_params* sp, tm_solve_info* infos, const char* who) {
+    if (!c || !a || !sigma || !y || !b || !sp || !infos) return fail(TM_ERR_ARG, "%s: null argument", who);
+    if ((((uintptr_t)y | (uintptr_t)b) & 15)) return fail(TM_ERR_ARG, "%s: fields must be 16-byte aligned", who);
+    return ms_check(c, op, n, sigma, sp, who);
+}
+
+extern "C" tm_status tm_rational_apply(tm_ctx* c, tm_op op, int n, double a0, const double* a, const double* sigma,
+                                       double* y, const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                                       void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(rational_args(c, op, n, a, sigma, y, b, sp, infos, "tm_rational_apply"));
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ms_prepare(c, sp, st));
+    const int nf = nflav(op);
+    const size_t sz = spinor_bytes(P64, 12 * nf, c->vh);
+    void *b64, *y64;
+    CKS(ws_get(c, WS_RAT + 0, sz, &b64));
+    CKS(ws_get(c, WS_RAT + 1, sz, &y64));
+    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
+    tm_status worst = TM_OK;
+    CKS(rational_native(c, op, n, a0, a, sigma, y64, b64, sp, infos, st, &worst));
+    CKS(stage_out(c, nf, y, WS_STAGE_X, y64, st));
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < n; ++k) infos[k].seconds = secs;
+    return worst;
+}
+
+template <int NF>
+static tm_status correction_core(tm_ctx* c, tm_op op, int n, double a0, const double* a, const double* sigma,
+                                 double p, double series_tol, int max_terms, void* y64, void* b64,
+                                 const tm_solve_params* sp, tm_solve_info* infos, int* napply, cudaStream_t st,
+                                 tm_status* worst) {
+    constexpr int NC = 12 * NF;
+    const size_t sz = spinor_bytes(P64, NC, c->vh);
+    void *t64, *u64, *w64, *te, *mid;
+    CKS(ws_get(c, WS_RAT + 2, sz, &t64));
+    CKS(ws_get(c, WS_RAT + 3, sz, &u64));
+    CKS(ws_get(c, WS_RAT + 4, sz, &w64));
+    CKS(ws_get(c, WS_APPLY_TE, sz, &te));
+    CKS(ws_get(c, WS_APPLY_MID, sz, &mid));
+    const long len = (long)c->vh * NC;
+    auto comb = [&](void* dst, double ca, const void* x, double cb, const void* v) -> tm_status {
+        LinComb lc{};
+        lc.n = 1;
+        lc.len = len;
+        lc.a0 = ca;
+        lc.b = reinterpret_cast<const double2*>(x);
+        lc.x[0] = reinterpret_cast<const double2*>(v);
+        lc.a[0] = cb;
+        lc.y = reinterpret_cast<double2*>(dst);
+        CK(launch_lincomb64(lc, st));
+        return TM_OK;
+    };
+    double bb = 0.0;
+    CKS((norm2_dev<P64, NC>(c, b64, st, &bb)));
+    CKS(comb(y64, 1.0, b64, 0.0, b64));
+    CKS(comb(t64, 1.0, b64, 0.0, b64));
+    double coef = 1.0;
+    *napply = 0;
+    for (int j = 1; j <= max_terms; ++j) {
+        // t <- Z t = A r(A)^2 t - t
+        CKS(rational_native(c, op, n, a0, a, sigma, u64, t64, sp, infos, st, worst));
+        CKS(rational_native(c, op, n, a0, a, sigma, w64, u64, sp, infos, st, worst));
+        CK((normal_op<P64, NF>(c, op, u64, w64, mid, te, st, nullptr, FIN_NONE)));
+        CKS(comb(t64, 1.0, u64, -1.0, t64));
+        ++*napply;
+        coef *= (p - (j - 1)) / j;
+        CKS(comb(y64, 1.0, y64, coef, t64));
+        double tt = 0.0;
+        CKS((norm2_dev<P64, NC>(c, t64, st, &tt)));
+        if (coef * coef * tt <= series_tol * series_tol * bb) break;
+    }
+    return TM_OK;
+}
+
+extern "C" tm_status tm_rational_correction(tm_ctx* c, tm_op op, int n, double a0, const double* a,
+                                            const double* sigma, double p, double series_tol, double* y,
+                                            const double* b, const tm_solve_params* sp, tm_solve_info* infos,
+                                            int* napply, void* stream) {
+    const auto t0 = std::chrono::steady_clock::now();
+    CKS(rational_args(c, op, n, a, sigma, y, b, sp, infos, "tm_rational_correction"));
+    if (!napply || !(series_tol > 0.0)) return fail(TM_ERR_ARG, "tm_rational_correction: bad argument");
+    const cudaStream_t st = c->sstream;
+    CKS(enter_solver(c, stream));
+    CKS(ms_prepare(c, sp, st));
+    const int nf = nflav(op);
+    const size_t sz = spinor_bytes(P64, 12 * nf, c->vh);
+    void *b64, *y64;
+    CKS(ws_get(c, WS_RAT + 0, sz, &b64));
+    CKS(ws_get(c, WS_RAT + 1, sz, &y64));
+    CKS(stage_in(c, nf, b, WS_STAGE_B, b64, st));
+    tm_status worst = TM_OK;
+    const int max_terms = 40;
+    CKS(nf == 1 ? correction_core<1>(c, op, n, a0, a, sigma, p, series_tol, max_terms, y64, b64, sp, infos,
+                                     napply, st, &worst)
+                : correction_core<2>(c, op, n, a0, a, sigma, p, series_tol, max_terms, y64, b64, sp, infos,
+                                     napply, st, &worst));
+    CKS(stage_out(c, nf, y, WS_STAGE_X, y64, st));
+    CK(cudaStreamSynchronize(st));
+    const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    for (int k = 0; k < n; ++k) infos[k].seconds = secs;
     return worst;
 }
 

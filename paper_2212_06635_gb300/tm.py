@@ -85,6 +85,13 @@ _sigs = {
     "tm_force_outer": [_vp, ct.c_int, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(_vp),
                        ct.POINTER(_vp), ct.c_int, _vp, _vp],
     "tm_apply_even": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_rational_inv_sqrt": [ct.c_int, ct.c_double, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                             ct.POINTER(ct.c_double), ct.POINTER(ct.c_double)],
+    "tm_rational_apply": [_vp, ct.c_int, ct.c_int, ct.c_double, ct.POINTER(ct.c_double), ct.POINTER(ct.c_double),
+                          _vp, _vp, ct.POINTER(tm_solve_params), ct.POINTER(tm_solve_info), _vp],
+    "tm_rational_correction": [_vp, ct.c_int, ct.c_int, ct.c_double, ct.POINTER(ct.c_double),
+                               ct.POINTER(ct.c_double), ct.c_double, ct.c_double, _vp, _vp,
+                               ct.POINTER(tm_solve_params), ct.POINTER(tm_solve_info), ct.POINTER(ct.c_int), _vp],
     "tm_field_norm2": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_field_norm2_noalloc": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_ptc_create": [ct.POINTER(_vp), ct.c_int, ct.POINTER(ct.c_int), ct.c_int],
@@ -239,6 +246,45 @@ def tm_solve_multishift(ctx, op, shifts, xs, b, sp, stream=None, check=True):
     if check:
         _check(st)
     return list(infos)
+
+
+def tm_rational_inv_sqrt(n, lo, hi):
+    """(a0, a[n], sigma[n], delta): Zolotarev's r(x) = a0 + sum a_k / (x + sigma_k) ~ x^-1/2 on [lo, hi]."""
+    a0 = ct.c_double()
+    a = (ct.c_double * n)()
+    s = (ct.c_double * n)()
+    d = ct.c_double()
+    _check(lib.tm_rational_inv_sqrt(int(n), float(lo), float(hi), ct.byref(a0), a, s, ct.byref(d)))
+    return a0.value, list(a), list(s), d.value
+
+
+def tm_rational_apply(ctx, op, coeffs, y, b, sp, stream=None, check=True):
+    """y = r(A) b for coeffs = (a0, a, sigma[, ...])."""
+    a0, a, sigma = coeffs[0], coeffs[1], coeffs[2]
+    n = len(a)
+    ap = (ct.c_double * n)(*a)
+    sg = (ct.c_double * n)(*sigma)
+    infos = (tm_solve_info * n)()
+    st = lib.tm_rational_apply(ctx, int(op), n, float(a0), ap, sg, ptr(y), ptr(b), ct.byref(sp), infos,
+                               _stream(stream))
+    if check:
+        _check(st)
+    return list(infos)
+
+
+def tm_rational_correction(ctx, op, coeffs, p, y, b, sp, series_tol=1e-14, stream=None, check=True):
+    """y = (1 + Z)^p b, Z = A r(A)^2 - 1; returns (infos, number of Z applications)."""
+    a0, a, sigma = coeffs[0], coeffs[1], coeffs[2]
+    n = len(a)
+    ap = (ct.c_double * n)(*a)
+    sg = (ct.c_double * n)(*sigma)
+    infos = (tm_solve_info * n)()
+    na = ct.c_int()
+    st = lib.tm_rational_correction(ctx, int(op), n, float(a0), ap, sg, float(p), float(series_tol), ptr(y),
+                                    ptr(b), ct.byref(sp), infos, ct.byref(na), _stream(stream))
+    if check:
+        _check(st)
+    return list(infos), na.value
 
 
 def tm_solve_batch(ctxs, op, sp, xs, bs, stream=None, check=True):

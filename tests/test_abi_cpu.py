@@ -52,3 +52,19 @@ def test_force_outer_host_checks(tm):
     assert "bad pointers" in tm.tm_last_error()
     with pytest.raises(ValueError):
         tm.tm_force_outer(None, 1, 2, [1.0, 2.0], [(0, 0)], [(0, 0)], 0)
+
+
+def test_rational_coefficients_match_oracle(tm):
+    """tm_rational_inv_sqrt (host code of the library) against the oracle's
+    Zolotarev coefficients, which are pinned by Chebyshev alternation."""
+    import numpy as np
+    from oracle import rational as RA
+    for n, lo, hi in ((4, 1e-3, 2.0), (8, 2.7e-5, 2.7), (12, 2.7e-5, 2.7), (16, 1e-6, 1.0)):
+        a0, a, s, d = tm.tm_rational_inv_sqrt(n, lo, hi)
+        b0, b, t, e = RA.zolotarev_inv_sqrt(n, lo, hi)
+        assert abs(a0 - b0) <= 1e-10 * b0
+        assert np.allclose(a, b, rtol=1e-9) and np.allclose(s, t, rtol=1e-9)
+        assert abs(d - e) <= 1e-6 * e
+    for bad in ((0, 1e-3, 1.0), (17, 1e-3, 1.0), (4, 0.0, 1.0), (4, 1.0, 0.5)):
+        with pytest.raises(tm.TMError):
+            tm.tm_rational_inv_sqrt(*bad)
