@@ -499,7 +499,7 @@ def run_rational(tm, args):
         coeffs = tm.tm_rational_inv_sqrt(CFG.N_SHIFTS, 1e-5 * lmax, lmax)
         out["delta"] = coeffs[3]
         ed = torch.from_numpy(eta.view(np.float64).copy()).cuda()
-        ee = float(torch.dot(ed, ed))
+        ee = float(torch.dot(ed.reshape(-1), ed.reshape(-1)))
         forms = (("double", tm.TM_F64, tm.TM_F64), ("single_single", tm.TM_F32, tm.TM_F64),
                  ("single_half", tm.TM_F32, tm.TM_F16))
         for name, sl, rf in forms:
@@ -512,7 +512,7 @@ def run_rational(tm, args):
             _sync()
             t1 = time.perf_counter()
             _, n2 = tm.tm_rational_correction(ctx, tm.TM_QH_SQ, coeffs, 0.5, acc, phi, sp, series_tol=1e-10)
-            energy = float(torch.dot(phi, acc))
+            energy = float(torch.dot(phi.reshape(-1), acc.reshape(-1)))
             _sync()
             t2 = time.perf_counter()
             out[name] = {"heatbath_s": round(t1 - t0, 4), "acceptance_s": round(t2 - t1, 4),

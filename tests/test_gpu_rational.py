@@ -114,8 +114,8 @@ def test_rational_full_size_properties():
         ay = torch.empty_like(bd)
         tm.tm_field_export(lat.ctx, tm.TM_F64, 2, ay, an)
         torch.cuda.synchronize()
-        yAy = float(torch.dot(y, ay))
-        bb = float(torch.dot(bd, bd))
+        yAy = float(torch.dot(y.reshape(-1), ay.reshape(-1)))
+        bb = float(torch.dot(bd.reshape(-1), bd.reshape(-1)))
         assert abs(yAy / bb - 1.0) <= 2.0 * delta + 1e-8, (yAy / bb - 1.0, delta)
         # solves to 1e-12 here: errors of 1e-10 sqrt(cond) per rational application
         # would move the energy by a few 1e-9
@@ -125,7 +125,7 @@ def test_rational_full_size_properties():
         acc = torch.zeros_like(bd)
         _, n2 = tm.tm_rational_correction(lat.ctx, tm.TM_QH_SQ, coeffs, 0.5, acc, phi, sp12, series_tol=1e-12)
         torch.cuda.synchronize()
-        energy = float(torch.dot(phi, acc))
+        energy = float(torch.dot(phi.reshape(-1), acc.reshape(-1)))
         assert abs(energy / bb - 1.0) <= 1e-9, energy / bb - 1.0
         assert n1 >= 1 and n2 >= 1
     finally:
