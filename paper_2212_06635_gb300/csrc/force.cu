@@ -10,10 +10,10 @@
 //                                            + ((1 + g_mu) Y_k(x+mu)) (x) X_k(x)^* ]
 //   force_mu(x) += T_A[ U_mu(x) W_mu(x) ]    (traceless anti-hermitian part)
 //
-// (optionally with g5 Y_k in place of Y_k, the form the Schur operators' force
-// takes)
 // so that force_mu(x) is the derivative of S = sum_k c_k Re <Y_k, H[U] X_k>
-// along su(3) directions of U_mu(x) (H the hopping term).
+// along su(3) directions of U_mu(x) (H the hopping term).  Optionally g5 Y_k
+// takes the place of Y_k: the Schur operators' hopping force is one such pair
+// per shift, X = (M_ee^-1 H_eo b, b) and Y = g5 (M_ee(-s)^-1 H_eo a, a).
 //
 // Each spin sum reduces to two spin components: in the chiral basis
 // g_mu = [[0, G], [G^+, 0]] and (1 + s g_mu) B = (h, s G^+ h) with
@@ -30,8 +30,7 @@
 // 32 half-site indices 32 b .. 32 b + 31 of both parities (z), one direction mu
 // per warp (y), so every warp's load of a field vector is one contiguous
 // 512-byte span (16 B per site) and its neighbour loads are the same span
-// shifted.  The four warps of one parity reuse X(x),
-// Y(x) through L1.
+// shifted.  The four warps of one parity reuse X(x), Y(x) through L1.
 //
 // Bytes per launch (algorithmic): each field read once (2 n V spinors), the FP32
 // links once (4 V x 12 reals), the force read and written once (2 x 4 V x 18 x 8).
