@@ -20,4 +20,6 @@ Paper: "Twisted mass ensemble generation on GPU machines" (arXiv 2212.06635).
   rational.py Zolotarev's rational approximation of A^-1/2, its application in
               partial fractions, and the binomial series of the correction
               term (Sec. 4.2, Fig. 4's heatbath and acceptance)
+  multigrid.py aggregation-based two-level multigrid preconditioner for GCR on
+              the full operator (Sec. 4.1's MG-preconditioned light solves)
 """
