@@ -68,3 +68,14 @@ def test_rational_coefficients_match_oracle(tm):
     for bad in ((0, 1e-3, 1.0), (17, 1e-3, 1.0), (4, 0.0, 1.0), (4, 1.0, 0.5)):
         with pytest.raises(tm.TMError):
             tm.tm_rational_inv_sqrt(*bad)
+
+
+def test_rational_coefficients_match_golden(tm):
+    import os
+    import numpy as np
+    path = os.path.join(ROOT, "tests", "golden", "zolotarev_n12_1e-5.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    a0, a, s, d = tm.tm_rational_inv_sqrt(12, 1e-5, 1.0)
+    assert abs(a0 - float(rows[0][0])) <= 1e-10 * a0
+    assert np.allclose(a, [float(r[0]) for r in rows[1:13]], rtol=1e-9)
+    assert np.allclose(s, [float(r[1]) for r in rows[1:13]], rtol=1e-9)

@@ -88,3 +88,23 @@ def test_correction_series_and_cancellation(dense_heavy, p):
         phi, _ = RA.binomial_series(-0.25, lambda v: Z @ v, b)
         acc, _ = RA.binomial_series(0.5, lambda v: Z @ v, phi)
         assert abs(np.vdot(phi, acc).real - np.vdot(b, b).real) <= 1e-12 * np.vdot(b, b).real
+
+
+def test_golden_zolotarev_coefficients():
+    """The stored coefficients (tests/golden/zolotarev_n12_1e-5.txt, written by
+    tests/golden/make_golden.py from this oracle) still come out, so a change of
+    the oracle's arithmetic shows here; and the stored approximation itself
+    equioscillates at 2n + 2 points."""
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "zolotarev_n12_1e-5.txt")
+    rows = [l.split() for l in open(path) if not l.startswith("#")]
+    a0 = float(rows[0][0])
+    a = np.array([float(r[0]) for r in rows[1:13]])
+    sigma = np.array([float(r[1]) for r in rows[1:13]])
+    delta = float(rows[13][0])
+    b0, b, s, d = RA.zolotarev_inv_sqrt(12, 1e-5, 1.0)
+    assert abs(b0 - a0) <= 1e-13 * a0
+    assert np.allclose(b, a, rtol=1e-12) and np.allclose(s, sigma, rtol=1e-12)
+    assert abs(d - delta) <= 1e-9 * delta
+    runs, peak = _alternations(a0, a, sigma, 1e-5, 1.0)
+    assert runs == 26 and abs(peak - delta) <= 1e-3 * delta
