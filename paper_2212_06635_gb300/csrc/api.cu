@@ -1390,9 +1390,12 @@ static tm_status correction_core(tm_ctx* c, tm_op op, int n, double a0, const do
     double coef = 1.0;
     *napply = 0;
     for (int j = 1; j <= max_terms; ++j) {
-        // t <- Z t = A r(A)^2 t - t
+        // t <- Z t = A r(A)^2 t - t; a failed multishift solve ends the series
+        // (its residual would poison every later term), returning the terms so far
         CKS(rational_native(c, op, n, a0, a, sigma, u64, t64, sp, infos, st, worst));
+        if (*worst != TM_OK) break;
         CKS(rational_native(c, op, n, a0, a, sigma, w64, u64, sp, infos, st, worst));
+        if (*worst != TM_OK) break;
         CK((normal_op<P64, NF>(c, op, u64, w64, mid, te, st, nullptr, FIN_NONE)));
         CKS(comb(t64, 1.0, u64, -1.0, t64));
         ++*napply;
