@@ -37,7 +37,7 @@ from synth import fields as F  # noqa: E402
 
 METRIC = "Mhat HBM GB/s (% peak); seconds to rel res 1e-10, chosen form vs plain FP64 CG"
 W = CFG.LIGHT_32
-CPU_SAMPLE_DIMS = (16, 16, 16, 32)
+CPU_SAMPLE_DIMS = (16, 16, 16, 16)
 ESZ = {0: 8, 1: 4, 2: 2, 3: 2}
 
 
@@ -158,11 +158,17 @@ def traffic_from_profile(kernel_tag):
 
 
 # ---------------------------------------------------------------------------
+# CPU baseline: the FP64 oracle as it stands, on the host cores
+# ---------------------------------------------------------------------------
+MHAT_FLOP_PER_SITE = 3792     # 2 Wilson hops (1320 each) + 2 6x6-pair matvecs (552 each) + axpy 48
+
+
 def cpu_oracle_steps(nsteps, dims=CPU_SAMPLE_DIMS):
     """Time the FP64 oracle applying M_hat^dag M_hat on a sub-lattice of the same
-    workload; returns (GB/s in FP64 algorithmic bytes, seconds per step)."""
+    workload in this process (one core); returns (GB/s in FP64 algorithmic
+    bytes, seconds per step)."""
     from oracle import dirac as D
-    u = F.gauge_field(dims, W.link_seed)
+    u = F.gauge_field(dims, W.link_seed, workers=1)
     op = D.TwistedMassClover(u, dims, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
     op.inv_even_light(+1)
     op.inv_even_light(-1)
@@ -178,21 +184,116 @@ def cpu_oracle_steps(nsteps, dims=CPU_SAMPLE_DIMS):
     return 2 * (k1 + k2) * vh / sec / 1e9, sec
 
 
+_CPU_BARRIER = None
+
+
+def _cpu_init(barrier):
+    global _CPU_BARRIER
+    _CPU_BARRIER = barrier
+
+
+def _cpu_replica(job):
+    """One host process: the oracle's M_hat^dag M_hat on its own right-hand side
+    (warmup untimed steps, then steps timed after every process is ready)."""
+    dims, rhs_seed, warmup, steps = job
+    from oracle import dirac as D
+    u = F.gauge_field(dims, W.link_seed, workers=1)
+    op = D.TwistedMassClover(u, dims, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
+    op.inv_even_light(+1)
+    op.inv_even_light(-1)
+    b = F.odd_spinor(dims, rhs_seed)
+    for _ in range(warmup):
+        op.MdagM(b)
+    _CPU_BARRIER.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        op.MdagM(b)
+    return time.perf_counter() - t0
+
+
+def cpu_oracle_parallel(warmup, steps, nproc=None, dims=CPU_SAMPLE_DIMS):
+    """The oracle on every host core: nproc spawned processes (one numpy thread
+    each) apply M_hat^dag M_hat to independent right-hand sides of the same
+    sub-lattice at the same time, the oracle's arithmetic unchanged.  Returns
+    (aggregate GB/s, processes, seconds of the slowest process per step)."""
+    import multiprocessing as mp
+    nproc = nproc or min(os.cpu_count() or 1, 32)
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        barrier = ctx.Barrier(nproc)
+        jobs = [(dims, W.rhs_seed + 100 * k, warmup, steps) for k in range(nproc)]
+        with ctx.Pool(nproc, initializer=_cpu_init, initargs=(barrier,)) as pool:
+            secs = pool.map(_cpu_replica, jobs, chunksize=1)
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    vh = int(np.prod(dims)) // 2
+    k1, k2 = mhat_bytes_per_site(0)
+    tmax = max(secs)
+    return nproc * steps * 2 * (k1 + k2) * vh / tmax / 1e9, nproc, tmax / steps
+
+
+def cpu_solve_4x4():
+    """Seconds of the oracle's FP64 CG on the 4^4 workload (M_hat^dag M_hat to
+    1e-12), one core, and its iteration count."""
+    from oracle import dirac as D
+    from oracle import solvers as S
+    w = CFG.LIGHT_4
+    op = D.TwistedMassClover(F.gauge_field(w.dims, w.link_seed, workers=1), w.dims, w.kappa, w.csw, mu=w.mu,
+                             bc_t=w.bc_t)
+    b = F.odd_spinor(w.dims, w.rhs_seed)
+    t0 = time.perf_counter()
+    op.inv_even_light(+1)
+    op.inv_even_light(-1)
+    x, it = S.cg(op.MdagM, b, tol=w.tol)
+    return time.perf_counter() - t0, it
+
+
+def cpu_baseline_record(args, fp64_iters=None):
+    """The cpu_baseline object: the oracle on all host cores (replicas of the
+    sub-lattice), one core alone, the 4^4 CPU solve, and the 32^3x64 FP64 CG
+    extrapolated from the one-core step time (labelled as such)."""
+    gbs, nproc, sec = cpu_oracle_parallel(1, 2)
+    gbs1, sec1 = cpu_oracle_steps(2)
+    s4, it4 = cpu_solve_4x4()
+    lat = "x".join(map(str, CPU_SAMPLE_DIMS))
+    rec = {"value": round(gbs, 4), "unit": "GB/s", "cores": nproc, "kind": "oracle",
+           "sample": f"FP64 numpy oracle as it stands, M_hat^dag M_hat on a {lat} sub-lattice of the same action: "
+                     f"{nproc} processes on independent right-hand sides, 2 timed steps each "
+                     f"({sec:.2f} s per step); host cores of this box",
+           "one_core": {"value": round(gbs1, 4), "unit": "GB/s", "seconds_per_step": round(sec1, 3)},
+           "host": {"cpu_count": os.cpu_count(), "machine": os.uname().machine},
+           "cpu_fp64_cg_4x4x4x4": {"seconds": round(s4, 3), "iters": it4, "tol": CFG.LIGHT_4.tol}}
+    if fp64_iters:
+        vol = W.volume / int(np.prod(CPU_SAMPLE_DIMS))
+        rec["cpu_fp64_cg_32x64_extrapolated"] = {
+            "seconds": round(sec1 * vol * fp64_iters, 1), "iters": fp64_iters,
+            "how": "extrapolated, not run: one-core step time x volume ratio x the GPU FP64 CG iteration count"}
+    return rec
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
-    nsteps = args.warmup + args.steps
     t0 = time.perf_counter()
-    gbs, sec = cpu_oracle_steps(nsteps)
+    gbs, nproc, sec = cpu_oracle_parallel(args.warmup, args.steps)
     wall = time.perf_counter() - t0
-    sample = (f"oracle (numpy FP64, one thread) M_hat^dag M_hat on a {'x'.join(map(str, CPU_SAMPLE_DIMS))} "
-              f"sub-lattice of the same action, {nsteps} steps")
+    sample = (f"oracle (numpy FP64, as it stands) M_hat^dag M_hat on a {'x'.join(map(str, CPU_SAMPLE_DIMS))} "
+              f"sub-lattice of the same action: {nproc} host processes on independent right-hand sides, "
+              f"{args.warmup} untimed + {args.steps} timed steps each")
     line = {"impl": "reference", "metric": METRIC, "value": round(gbs, 4), "unit": "GB/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec * 1e3, 2),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": W.name, "lattice": list(CPU_SAMPLE_DIMS),
-                                            "step": "M_hat^dag M_hat (2 M_hat), FP64 oracle"},
-            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                                            "step": "M_hat^dag M_hat (2 M_hat), FP64 oracle, one per host process"},
+            "gflops": round(gbs / (2 * sum(mhat_bytes_per_site(0))) * 2 * MHAT_FLOP_PER_SITE, 4),
+            "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": nproc, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
             "wall_s": round(wall, 1)}
@@ -342,11 +443,11 @@ def run_ours(args, rank, world, local_rank):
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
-        gbs, sec = cpu_oracle_steps(3)
-        cpu = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-               "sample": f"FP64 numpy oracle, M_hat^dag M_hat on a {'x'.join(map(str, CPU_SAMPLE_DIMS))} "
-                         f"sub-lattice of the same action, 3 steps of {sec:.2f} s, host cores of this box"}
+        cpu = cpu_baseline_record(args, tts.get("fp64_cg", {}).get("iters"))
     if rank == 0:
+        # the full per-workload records go on their own line before the headline,
+        # so that the headline (the last line) stays short
+        print(json.dumps({"workloads": extra}), flush=True)
         line = {
             "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(ms / args.steps, 4), "higher_is_better": True,
@@ -358,10 +459,12 @@ def run_ours(args, rank, world, local_rank):
                        "l2": "inputs larger than L2 (%.2f GB per step vs 0.13 GB L2)" % (step_bytes / 1e9),
                        "parallelism": f"replicas{world}" if world > 1 else "single GPU"},
             "frac_of_peak": round(value / peak, 4),
+            "gflops": round(world * 2 * MHAT_FLOP_PER_SITE * vh * args.steps / (ms * 1e-3) / 1e9, 1),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "traffic": traffic, "kernel": dom,
                          "kernel_ms": round(dms, 5), "peak_kind": peak_kind},
             "time_to_solution": tts,
+            "workload_summary": summarize(extra),
             "cpu_baseline": cpu,
             "e2e": {"value": round(e2e, 2), "unit": "GB/s", "h2d_bytes_per_step": vh * 24 * 8,
                     "d2h_bytes_per_step": vh * 24 * 8},
@@ -369,10 +472,41 @@ def run_ours(args, rank, world, local_rank):
             "clocks": clocks,
             "tuning": {"even_pass": "staged" if tuning[0] else "direct",
                        "odd_pass": "staged" if tuning[1] else "direct"},
-            "workloads": extra,
         }
         print(json.dumps(line), flush=True)
     return 0
+
+
+def summarize(extra):
+    """Seconds to solution of each extra workload, a few numbers per workload."""
+    out = {}
+    ms = extra.get("multishift_heavy_24x48", {})
+    if "single_refined" in ms:
+        out["multishift_24x48_s"] = {k: ms[k]["seconds"] for k in
+                                     ("single_refined", "single_half_refined", "half_refined", "double") if k in ms}
+    bt = extra.get("batch_uneven_24", {})
+    if "batched_s" in bt:
+        out["batch_24_s"] = {"batched": bt["batched_s"], "sequential": bt.get("sequential_s")}
+    fo = extra.get("force_outer_heavy_24x48", {})
+    if "f32_fields" in fo:
+        out["force_outer_24x48_frac_of_hbm"] = {k: fo[k]["frac_of_hbm"] for k in ("f32_fields", "f16_fields")}
+    ra = extra.get("rational_correction_heavy_24x48", {})
+    if "double" in ra:
+        out["rational_heatbath_24x48_s"] = {k: ra[k]["heatbath_s"] for k in ("double", "single_single", "single_half")
+                                            if k in ra}
+    pt = extra.get("ptc_fcg_48x96", {})
+    if "ptc_fcg" in pt:
+        out["ptc_48x96"] = {"train_pairs": pt.get("train_pairs"), "train_configs": pt.get("train_configs"),
+                            "train_s": pt.get("train_s"), "ptc_fcg_s": round(pt["ptc_fcg"]["seconds"], 3),
+                            "ptc_fcg_iters": pt["ptc_fcg"]["iters"],
+                            "mixed_cg_f16_s": round(pt["mixed_cg_f16"]["seconds"], 3),
+                            "fp64_cg_s": round(pt["fp64_cg"]["seconds"], 3)}
+    elif "error" in pt:
+        out["ptc_48x96"] = {"error": pt["error"][:200]}
+    mg = extra.get("mg_gcr_48x96", {})
+    if mg:
+        out["mg_48x96"] = {k: v for k, v in mg.items() if k.endswith("_s") or k.endswith("_iters")}
+    return out
 
 
 def _sync():
@@ -467,12 +601,12 @@ def run_force(args, peak):
     """The rational-approximation force step on the heavy doublet at 24^3x48: the
     outer products of 12 two-flavour field pairs (one per shift) on every link,
     one tm_force_outer launch, fields in FP32 and in FP16 storage."""
-    from paper_2212_06635_gb300.kernel_probe import force_probe
+    from paper_2212_06635_gb300.kernel_timing import force_outer
     dims = CFG.HEAVY_24.dims
     out = {"lattice": list(dims), "pairs": CFG.N_SHIFTS, "flavours": 2,
            "bytes": "2 n V field sites + FP32 links + FP64 force read and written"}
     for name, prec in (("f32_fields", 1), ("f16_fields", 3)):
-        ms, b = force_probe(dims, prec, 2, CFG.N_SHIFTS, 20, quiet=True)
+        ms, b = force_outer(dims, prec, 2, CFG.N_SHIFTS, 20, quiet=True)
         out[name] = {"us_per_launch": round(ms * 1e3, 2), "gb_per_launch": round(b / 1e9, 4),
                      "gbs": round(b / ms / 1e6, 1), "frac_of_hbm": round(b / ms / 1e6 / peak, 4)}
     return out
@@ -597,16 +731,16 @@ def main():
                     help="skip the heavy multishift and uneven batch workloads")
     ap.add_argument("--no-ptc", action="store_true",
                     help="skip the PTC training + PTC-FCG workload on 48^3x96")
-    ap.add_argument("--ptc", action="store_true",
-                    help="full PTC training (2048 pairs from 8 configurations, several minutes) "
-                         "instead of the default 512 pairs from 2 configurations")
+    ap.add_argument("--ptc-quick", action="store_true",
+                    help="short PTC training (512 pairs from 2 configurations) instead of the workload's "
+                         "2048 pairs from 8 configurations")
     ap.add_argument("--ptc-pairs", type=int, default=None)
     ap.add_argument("--ptc-configs", type=int, default=None)
     args = ap.parse_args()
     if args.ptc_pairs is None:
-        args.ptc_pairs = 2048 if args.ptc else 512
+        args.ptc_pairs = 512 if args.ptc_quick else 2048
     if args.ptc_configs is None:
-        args.ptc_configs = 8 if args.ptc else 2
+        args.ptc_configs = 2 if args.ptc_quick else 8
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
     world = int(os.environ.get("WORLD_SIZE", "1"))
