@@ -156,19 +156,23 @@ tm_status tm_field_export(tm_ctx* ctx, tm_prec prec, int nflavour, double* dst_c
 tm_status tm_field_norm2(tm_ctx* ctx, tm_prec prec, int nflavour, const void* field, double* result,
                          void* stream);
 
-/* Allocation-free variant of tm_field_norm2, for callers that may not allocate
- * device memory at call time (code running during CUDA-graph stream capture,
- * latency-critical loops that must not reach the allocator, frameworks that own
- * the device memory budget).  The paper has no counterpart: this is a library
- * service, not part of the method.  Same arguments, result and reduction order
- * as tm_field_norm2, but the block partials live in a fixed array in the
- * library's device memory (about 512 KB, held by every GPU that loads the
- * library until exit) instead of the context's scratch.  Limit: at most
- * 16,777,216 sites per parity (TM_ERR_ARG beyond).  The first call on a device
- * looks up that array's device address, so make the first call before any stream
- * capture.  All calls share the array: calls whose executions overlap on the GPU
- * (different streams, or different contexts on one device) race and give wrong
- * results.  Allocates nothing. */
+/* Allocation-free variant of tm_field_norm2, for callers that cannot allocate
+ * device memory when they need a norm: a host framework that has reserved the
+ * whole device memory budget for its own pool (a side cudaMalloc would fail or
+ * take memory already promised elsewhere), or a latency-critical loop that must
+ * never reach the device allocator (cudaMalloc / cudaFree can synchronise the
+ * device).  The paper has no counterpart: this is a library service, not part of
+ * the method.  Same arguments, result and reduction order as tm_field_norm2, but
+ * the block partials live in a fixed array in the library's device memory (about
+ * 512 KB, held by every GPU that loads the library until exit) instead of the
+ * context's scratch.  Limit: at most 16,777,216 sites per parity (TM_ERR_ARG
+ * beyond).  field and result must be device pointers (TM_ERR_ARG otherwise,
+ * before any launch).  The first call on a device looks up that array's device
+ * address, so make the first call before any stream capture.  All calls share
+ * the array, which keeps the last call's partial sums (each call overwrites the
+ * ones it reads and zeroes the counter first): calls whose executions overlap on
+ * the GPU (different streams, or different contexts on one device) race and give
+ * wrong results.  Calls no cudaMalloc, cudaFree or allocating library routine. */
 tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, const void* field,
                                  double* result, void* stream);
 

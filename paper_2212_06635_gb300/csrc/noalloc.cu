@@ -1,13 +1,13 @@
 // tm_field_norm2_noalloc: the squared-norm reduction of tm_field_norm2 for
-// callers that must not allocate device memory at call time.
+// callers that cannot allocate device memory when they need a norm.
 //
-// Some callers cannot call cudaMalloc when they need a norm:
-// - code running while a stream is being captured into a CUDA graph, where a
-//   plain cudaMalloc is not permitted;
-// - latency-critical loops that must never reach the device allocator, because
-//   an allocation can synchronise the device;
-// - host frameworks that own the whole device memory budget through their own
-//   pool.
+// Who cannot allocate, and why:
+// - a host framework that has reserved the whole device memory budget for its
+//   own pool allocator: a side cudaMalloc from a library either fails outright
+//   or takes memory the pool has already promised elsewhere;
+// - a latency-critical loop (a solver driven from an outer integrator, a serving
+//   step) that must never reach the device allocator, because cudaMalloc and
+//   cudaFree can synchronise the whole device.
 // The existing tm_field_norm2 keeps its block partials in reduction scratch that
 // tm_create allocated; this variant keeps them instead in a fixed array in the
 // library's own device memory (below), so a call allocates nothing.
@@ -15,7 +15,9 @@
 // The array is NOALLOC_MAX_BLOCKS partial sums plus the last-block counter
 // (about 512 KB). Every GPU that loads the library holds it until the process
 // exits. Fields are limited to NOALLOC_MAX_BLOCKS * BLAS_BS = 16,777,216 sites
-// per parity; larger fields are rejected with TM_ERR_ARG.
+// per parity; larger fields are rejected with TM_ERR_ARG. The field and the
+// result must be device memory: other pointers are rejected with TM_ERR_ARG
+// before anything is launched.
 #include <mutex>
 
 #include "tm_host.h"
@@ -32,6 +34,17 @@ constexpr int NOALLOC_MAX_BLOCKS = 65536;
 static __device__ __align__(256) double tm_noalloc_scratch[NOALLOC_MAX_BLOCKS + 32];
 
 static std::mutex g_noalloc_mu;
+
+// device (or managed) memory, as the kernel needs; cudaPointerGetAttributes
+// allocates nothing
+static bool noalloc_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
 static double* g_noalloc_addr[256] = {};   // device address of the array, per device ordinal
 
 // Device address of the scratch array on the current device (looked up once per
@@ -80,6 +93,8 @@ extern "C" tm_status tm_field_norm2_noalloc(const tm_ctx* c, tm_prec prec, int n
                             "use tm_field_norm2");
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) return tmk_fail_msg(TM_ERR_CUDA, cudaGetErrorString(e));
+    if (!noalloc_device_ptr(field) || !noalloc_device_ptr(result))
+        return tmk_fail_msg(TM_ERR_ARG, "tm_field_norm2_noalloc: field and result must be device pointers");
     double* scratch = nullptr;
     const tm_status s = noalloc_scratch(c->device, &scratch);
     if (s != TM_OK) return s;
