@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dirac as D
 from synth import fields as F
-from tests.gpu_util import PREC_TOL, Lat, rel, tol
+from tests.gpu_util import Lat, rel, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -73,23 +73,48 @@ def test_periodic_time_boundary():
         lat.close()
 
 
-def test_full_size_sampled_32x64():
-    """32^3x64 (the mixed-precision CG workload) in the launch configuration the
-    benchmark uses: FP64 and FP32 Q_hat_+ checked at sampled odd sites."""
+def _two_hop_odd(geo, odd_idx):
+    """Odd-list indices of the odd sites within two hops (odd -> even -> odd) of
+    the given odd sites: the support of Q_hat at those sites."""
+    S = geo.odd[np.asarray(odd_idx)]
+    e = np.unique(np.concatenate([geo.fwd[m][S] for m in range(4)] + [geo.bwd[m][S] for m in range(4)]))
+    o = np.unique(np.concatenate([geo.fwd[m][e] for m in range(4)] + [geo.bwd[m][e] for m in range(4)]))
+    return o // 2
+
+
+@pytest.fixture(scope="module")
+def full32():
+    """32^3x64, the mixed-precision CG workload, and 67 sampled odd sites."""
     dims = (32, 32, 32, 64)
     u = F.gauge_field(dims, 1001)
     op = D.TwistedMassClover(u, dims, 0.1400, CSW, mu=0.0015)
     lat = Lat(u, dims, 0.1400, CSW, mu=0.0015)
-    try:
-        psi = F.odd_spinor(dims, 2001)
-        rng = np.random.default_rng(5)
-        s = np.unique(np.concatenate([[0, 1, lat.vh - 1], rng.integers(0, lat.vh, 64)]))
-        ref = op.Qhat_at(psi, s, +1)
-        for prec in (0, 1):
-            got = lat.apply(lat.tm.TM_QHAT_PLUS, prec, psi)[s]
-            assert rel(got, ref) < PREC_TOL[prec], (prec, rel(got, ref))
-    finally:
-        lat.close()
+    psi = F.odd_spinor(dims, 2001)
+    rng = np.random.default_rng(5)
+    s = np.unique(np.concatenate([[0, 1, lat.vh - 1], rng.integers(0, lat.vh, 64)]))
+    # M_hat^dag M_hat = Q_hat_- Q_hat_+ at s needs Q_hat_+ psi on the odd sites
+    # within two hops of s; the oracle evaluates it there only
+    n2 = _two_hop_odd(op.geo, s)
+    mid = np.zeros_like(psi)
+    mid[n2] = op.Qhat_at(psi, n2, +1)
+    refs = {"qp": op.Qhat_at(psi, s, +1), "mdagm": op.Qhat_at(mid, s, -1)}
+    yield lat, psi, s, refs
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3, 2], ids=["f64", "f32", "f16", "bf16"])
+def test_full_size_sampled_32x64(full32, prec):
+    """32^3x64 in the launch configuration the benchmark uses (autotuned
+    variant, every storage precision): Q_hat_+ and M_hat^dag M_hat checked at
+    sampled odd sites, including the first and the last."""
+    lat, psi, s, refs = full32
+    tm = lat.tm
+    if prec != 0:
+        tm.tm_autotune(lat.ctx, prec, 1)
+    got = lat.apply(tm.TM_QHAT_PLUS, prec, psi)[s]
+    assert rel(got, refs["qp"]) < tol(prec), (prec, rel(got, refs["qp"]))
+    got = lat.apply(tm.TM_MDAGM, prec, psi)[s]
+    assert rel(got, refs["mdagm"]) < tol(prec, 2), (prec, rel(got, refs["mdagm"]))
 
 
 @pytest.mark.parametrize("prec", [1, 3, 2], ids=["f32", "f16", "bf16"])
