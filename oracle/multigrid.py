@@ -18,7 +18,8 @@ type operators, applied to the full operator M of oracle.dirac:
   upper two and the lower two spins), so that the coarse operator keeps
   gamma_5-hermiticity;
 * prolongator P: on every aggregate, the restrictions of the nvec vectors,
-  orthonormalised (Gram-Schmidt); P^+ P = 1;
+  orthonormalised (Gram-Schmidt, i.e. the QR factorisation whose R has a
+  positive real diagonal, which fixes each column's phase); P^+ P = 1;
 * coarse operator M_c = P^+ M P (Galerkin), nearest-neighbour on the block
   lattice;
 * preconditioner: coarse-grid correction z = P M_c^-1 P^+ r followed by nu
@@ -84,7 +85,9 @@ class TwoLevelMG:
     """Two-level Galerkin multigrid preconditioner for op.M (full lattice, one flavour)."""
 
     def __init__(self, op: D.TwistedMassClover, block, nvec, setup_steps=30, smooth_steps=4, seed=0,
-                 sign=+1, vectors=None):
+                 sign=+1, vectors=None, init=None):
+        """vectors: ready near-null vectors (no setup); init: the nvec random
+        starting fields of the setup (drawn from seed when None)."""
         self.op = op
         self.sign = sign
         self.agg = Aggregates(op.geo, block)
@@ -94,8 +97,11 @@ class TwoLevelMG:
         if vectors is None:
             gen = np.random.default_rng(seed)
             vectors = []
-            for _ in range(nvec):
-                v = gen.standard_normal((V, 4, 3)) + 1j * gen.standard_normal((V, 4, 3))
+            for j in range(nvec):
+                if init is None:
+                    v = gen.standard_normal((V, 4, 3)) + 1j * gen.standard_normal((V, 4, 3))
+                else:
+                    v = np.array(init[j], dtype=np.complex128).reshape(V, 4, 3)
                 v = minimal_residual(self.apply, np.zeros_like(v), v, setup_steps)
                 vectors.append(v / np.linalg.norm(v))
         self.vectors = vectors
@@ -105,7 +111,9 @@ class TwoLevelMG:
             s = self.agg.sites_of_block[k]
             for h in range(2):
                 cols = np.stack([v[s][:, 2 * h:2 * h + 2, :].reshape(-1) for v in vectors], axis=1)
-                q, _ = np.linalg.qr(cols)          # Gram-Schmidt on the aggregate
+                q, r = np.linalg.qr(cols)
+                d = np.diag(r)
+                q = q * (d / np.abs(d))[None, :]   # Gram-Schmidt: R with a positive diagonal
                 self.P.append(q)
         self.ncoarse = len(self.P) * nvec
         self._Mc = None

@@ -96,3 +96,21 @@ def test_multigrid_gain():
     for x in (x0, x1):
         assert np.linalg.norm(b - mg.apply(x)) <= 1.01e-8 * np.linalg.norm(b)
     assert it1 * 4 < it0, (it0, it1)
+
+
+def test_prolongator_is_gram_schmidt(mg44):
+    """Each aggregate's columns are the Gram-Schmidt orthonormalisation of the
+    restricted near-null vectors: P_a^+ V_a is upper triangular with a positive
+    real diagonal (the unique QR factor with that property), so the columns'
+    phases are fixed by the vectors alone."""
+    op, mg = mg44
+    for a, q in enumerate(mg.P):
+        k, h = divmod(a, 2)
+        s = mg.agg.sites_of_block[k]
+        cols = np.stack([v[s][:, 2 * h:2 * h + 2, :].reshape(-1) for v in mg.vectors], axis=1)
+        r = q.conj().T @ cols
+        assert np.allclose(q.conj().T @ q, np.eye(mg.nvec), atol=1e-12)
+        assert np.max(np.abs(np.tril(r, -1))) < 1e-12 * np.max(np.abs(r))
+        d = np.diag(r)
+        assert np.all(d.real > 0) and np.max(np.abs(d.imag)) < 1e-12 * np.max(np.abs(d))
+        assert np.linalg.norm(q @ r - cols) < 1e-12 * np.linalg.norm(cols)
