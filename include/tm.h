@@ -359,6 +359,82 @@ tm_status tm_ptc_load(tm_ptc* net, const char* path);
 tm_status tm_solve_fcg(tm_ctx* ctx, tm_op op, tm_ptc* net, const tm_solve_params* sp, double* x,
                        const double* b, tm_solve_info* info, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Two-level multigrid on the full operator (Sec. 4.1: the light sector's most
+ * poorly conditioned solves run an outer GCR preconditioned by multigrid, about a
+ * hundred times faster than mixed-precision CG at the physical mass; the paper
+ * gives no detail of the method).  The library builds the textbook
+ * aggregation-based Galerkin form for Wilson-type operators:
+ *   aggregates   the lattice cut into blocks of block[0..3] sites, each block split
+ *                by chirality (spins 0,1 / spins 2,3): aggregate a = 2 k + h, k the
+ *                block's lexicographic index on the block lattice
+ *                ((kt*nz + kz)*ny + ky)*nx + kx;
+ *   near-null    nvec fields given by the caller (random fields), each smoothed by
+ *                setup_steps minimal-residual steps on M v = 0 and normalised;
+ *   prolongator  per aggregate, the Gram-Schmidt orthonormalisation (R with a
+ *                positive real diagonal) of the vectors' restrictions; P^+ P = 1;
+ *   coarse op.   M_c = P^+ M P, nearest neighbour on the block lattice;
+ *   precond.     z = P M_c^-1 P^+ r, the coarse system solved by restarted GCR to
+ *                relative residual coarse_tol (the exact coarse solve is the limit
+ *                coarse_tol -> 0), then smooth_steps minimal-residual steps on
+ *                M z = r starting from that z.
+ * Canonical full field: FP64 [t][z][y][x][spin 4][colour 3] (re, im), every
+ * lattice site, device memory, 16-byte aligned.  Coarse vector: complex FP64
+ * [a][j], a = 2 k + h, j < nvec (tm_mg_coarse_size complex entries).
+ * The multigrid keeps the gauge generation and clover stamp of its setup; calls
+ * after tm_gauge_load or a new tm_clover_compute return TM_ERR_STALE until the
+ * next tm_mg_setup.
+ * ------------------------------------------------------------------------- */
+typedef struct tm_mg tm_mg;
+
+typedef struct {
+    int block[4];        /* aggregate block extents (X, Y, Z, T), each dividing the lattice extent */
+    int nvec;            /* near-null vectors: 1 .. 16 and at most 6 x block volume */
+    int setup_steps;     /* minimal-residual steps per near-null vector */
+    int smooth_steps;    /* minimal-residual post-smoothing steps of the preconditioner */
+    int sign;            /* +1: M(+mu), -1: M(-mu) */
+    tm_prec prec;        /* TM_F64 or TM_F32: storage and arithmetic of the setup, the
+                            prolongator, the coarse operator and the preconditioner;
+                            reductions are FP64 either way */
+    double coarse_tol;   /* relative residual of the coarse GCR solve (> 0) */
+    int coarse_maxiter;  /* bound on coarse GCR iterations per preconditioner application */
+    int coarse_restart;  /* coarse GCR restart length, 1 .. 16 */
+} tm_mg_params;
+
+/* out = M(sign) in, the full (unpreconditioned) operator of the conventions above
+ * on canonical full fields (device), in storage and arithmetic prec (TM_F64 or
+ * TM_F32).  Stream-ordered.  TM_ERR_STALE without a current clover term. */
+tm_status tm_apply_full(tm_ctx* ctx, int sign, tm_prec prec, double* out, const double* in, void* stream);
+/* Allocates the hierarchy's device memory for ctx's lattice (prolongator
+ * 12 V nvec complex, coarse operator 36 nvec^2 complex per block, the near-null
+ * fields and the coarse solver's vectors).  The context must outlive it. */
+tm_status tm_mg_create(tm_mg** mg, tm_ctx* ctx, const tm_mg_params* params);
+tm_status tm_mg_destroy(tm_mg* mg);
+tm_status tm_mg_coarse_size(const tm_mg* mg, size_t* n_complex);
+/* Setup from nvec canonical full fields stored back to back at init (device):
+ * smoothing, prolongator, coarse operator.  Synchronous. */
+tm_status tm_mg_setup(tm_mg* mg, const double* init, void* stream);
+/* The smoothed, normalised near-null vectors: nvec canonical full fields back to back (device). */
+tm_status tm_mg_vectors(tm_mg* mg, double* out, void* stream);
+/* fine = P coarse;  coarse = P^+ fine;  out = M_c in.  Device vectors, stream-ordered. */
+tm_status tm_mg_prolong(tm_mg* mg, double* fine, const double* coarse, void* stream);
+tm_status tm_mg_restrict(tm_mg* mg, double* coarse, const double* fine, void* stream);
+tm_status tm_mg_coarse_apply(tm_mg* mg, double* out, const double* in, void* stream);
+/* z = the preconditioner applied to r (canonical full fields, device); the coarse
+ * GCR iterations it took go to *coarse_iters (may be NULL).  Synchronous. */
+tm_status tm_mg_precondition(tm_mg* mg, double* z, const double* r, int* coarse_iters, void* stream);
+/* Solve M(sign) x = b (canonical full fields, device; x in: initial guess, out:
+ * solution) to FP64 true relative residual sp->tol.  The outer loop recomputes
+ * r = b - M x with the FP64 operator; until converged, a restarted flexible GCR
+ * (restart sp->chunk, 0 = 8, at most 16) in the multigrid's precision, or in
+ * sp->sloppy (TM_F64 / TM_F32) without one, preconditioned by mg (NULL: none),
+ * solves M e = r / ||r|| to relative residual sp->delta (<= 0: 1e-5; FP64 inner
+ * solves aim at the outer target directly) and x += ||r|| e.  info->iters counts
+ * GCR iterations, info->reliable_updates the outer corrections.  mg must belong to
+ * ctx and the same sign.  Synchronous. */
+tm_status tm_solve_gcr(tm_ctx* ctx, int sign, tm_mg* mg, const tm_solve_params* sp, double* x,
+                       const double* b, tm_solve_info* info, void* stream);
+
 /* Stencil kernel variant of each pass of the Schur operator for one storage
  * precision and flavour count: 0 = direct (operands loaded into registers),
  * 1 = shared-memory staged (asynchronous copies of the neighbour spinors, links

@@ -175,7 +175,7 @@ extern "C" tm_status tm_destroy(tm_ctx* c) {
     for (int p = 0; p < 2; ++p) { cudaFree(c->gauge64[p]); cudaFree(c->clovA64[p]); }
     for (int q = 0; q < 4; ++q) {
         cudaFree(c->gaugeP[q][0]); cudaFree(c->gaugeP[q][1]);
-        cudaFree(c->clovAP[q]); cudaFree(c->clovBP[q]); cudaFree(c->clovHP[q]);
+        cudaFree(c->clovAP[q]); cudaFree(c->clovBP[q]); cudaFree(c->clovHP[q]); cudaFree(c->clovAeP[q]);
     }
     cudaFree(c->clovB64); cudaFree(c->clovH64);
     cudaFree(c->partial); cudaFree(c->counter); cudaFree(c->ctl); cudaFree(c->ms); cudaFree(c->d_scal);
@@ -2292,4 +2292,16 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
 namespace tmk {
 // record an error message for tm_last_error from another translation unit
 tm_status tmk_fail_msg(tm_status s, const char* msg) { return fail(s, "%s", msg); }
+
+// for the other translation units (multigrid): error messages, precision copies
+// of the links and clover terms, context workspace
+tm_status tmk_failf(tm_status s, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return s;
+}
+tm_status tmk_ensure_prec(tm_ctx* c, int P, cudaStream_t st) { return ensure_prec(c, P, st); }
+tm_status tmk_ws_get(tm_ctx* c, int id, size_t bytes, void** out) { return ws_get(c, id, bytes, out); }
 }  // namespace tmk

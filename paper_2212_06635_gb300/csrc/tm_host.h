@@ -37,6 +37,9 @@ struct tm_ctx {
     void* clovBP[4] = {};
     void* clovHP[4] = {};
     long clovP_stamp[4] = {0, 0, 0, 0};
+    // even-site A in a storage precision, made only for the full operator (multigrid)
+    void* clovAeP[4] = {};
+    long clovAeP_stamp[4] = {0, 0, 0, 0};
 
     // reduction scratch and control words
     double* partial = nullptr;

@@ -50,6 +50,12 @@ class tm_tuning(ct.Structure):
     _fields_ = [("even_pass", ct.c_int), ("odd_pass", ct.c_int)]
 
 
+class tm_mg_params(ct.Structure):
+    _fields_ = [("block", ct.c_int * 4), ("nvec", ct.c_int), ("setup_steps", ct.c_int), ("smooth_steps", ct.c_int),
+                ("sign", ct.c_int), ("prec", ct.c_int), ("coarse_tol", ct.c_double), ("coarse_maxiter", ct.c_int),
+                ("coarse_restart", ct.c_int)]
+
+
 class TMError(RuntimeError):
     def __init__(self, status, msg):
         super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
@@ -109,6 +115,17 @@ _sigs = {
     "tm_ptc_save": [_vp, ct.c_char_p],
     "tm_ptc_load": [_vp, ct.c_char_p],
     "tm_solve_fcg": [_vp, ct.c_int, _vp, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
+    "tm_apply_full": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_mg_create": [ct.POINTER(_vp), _vp, ct.POINTER(tm_mg_params)],
+    "tm_mg_destroy": [_vp],
+    "tm_mg_coarse_size": [_vp, ct.POINTER(ct.c_size_t)],
+    "tm_mg_setup": [_vp, _vp, _vp],
+    "tm_mg_vectors": [_vp, _vp, _vp],
+    "tm_mg_prolong": [_vp, _vp, _vp, _vp],
+    "tm_mg_restrict": [_vp, _vp, _vp, _vp],
+    "tm_mg_coarse_apply": [_vp, _vp, _vp, _vp],
+    "tm_mg_precondition": [_vp, _vp, _vp, ct.POINTER(ct.c_int), _vp],
+    "tm_solve_gcr": [_vp, ct.c_int, _vp, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
     "tm_autotune": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning), _vp],
     "tm_set_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
     "tm_get_tuning": [_vp, ct.c_int, ct.c_int, ct.POINTER(tm_tuning)],
@@ -423,6 +440,69 @@ def tm_ptc_load(net, path):
 def tm_solve_fcg(ctx, op, net, sp, x, b, stream=None, check=True):
     info = tm_solve_info()
     st = lib.tm_solve_fcg(ctx, int(op), net, ct.byref(sp), ptr(x), ptr(b), ct.byref(info), _stream(stream))
+    if check:
+        _check(st)
+    return info
+
+
+# ---------------------------------------------------------------------------
+# two-level multigrid on the full operator
+# ---------------------------------------------------------------------------
+def mg_params(block, nvec, setup_steps=20, smooth_steps=4, sign=1, prec=TM_F32, coarse_tol=0.05,
+              coarse_maxiter=200, coarse_restart=16):
+    return tm_mg_params((ct.c_int * 4)(*block), nvec, setup_steps, smooth_steps, sign, prec, coarse_tol,
+                        coarse_maxiter, coarse_restart)
+
+
+def tm_apply_full(ctx, sign, prec, out, inp, stream=None):
+    _check(lib.tm_apply_full(ctx, int(sign), int(prec), ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_mg_create(ctx, params):
+    h = _vp()
+    _check(lib.tm_mg_create(ct.byref(h), ctx, ct.byref(params)))
+    return h.value
+
+
+def tm_mg_destroy(mg):
+    _check(lib.tm_mg_destroy(mg))
+
+
+def tm_mg_coarse_size(mg):
+    n = ct.c_size_t()
+    _check(lib.tm_mg_coarse_size(mg, ct.byref(n)))
+    return n.value
+
+
+def tm_mg_setup(mg, init, stream=None):
+    _check(lib.tm_mg_setup(mg, ptr(init), _stream(stream)))
+
+
+def tm_mg_vectors(mg, out, stream=None):
+    _check(lib.tm_mg_vectors(mg, ptr(out), _stream(stream)))
+
+
+def tm_mg_prolong(mg, fine, coarse, stream=None):
+    _check(lib.tm_mg_prolong(mg, ptr(fine), ptr(coarse), _stream(stream)))
+
+
+def tm_mg_restrict(mg, coarse, fine, stream=None):
+    _check(lib.tm_mg_restrict(mg, ptr(coarse), ptr(fine), _stream(stream)))
+
+
+def tm_mg_coarse_apply(mg, out, inp, stream=None):
+    _check(lib.tm_mg_coarse_apply(mg, ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_mg_precondition(mg, z, r, stream=None):
+    it = ct.c_int()
+    _check(lib.tm_mg_precondition(mg, ptr(z), ptr(r), ct.byref(it), _stream(stream)))
+    return it.value
+
+
+def tm_solve_gcr(ctx, sign, mg, sp, x, b, stream=None, check=True):
+    info = tm_solve_info()
+    st = lib.tm_solve_gcr(ctx, int(sign), mg, ct.byref(sp), ptr(x), ptr(b), ct.byref(info), _stream(stream))
     if check:
         _check(st)
     return info
