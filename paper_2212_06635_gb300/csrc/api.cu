@@ -325,9 +325,10 @@ static const void* clovH_ptr(const tm_ctx* c, int P) { return P == P64 ? (const 
 // ---------------------------------------------------------------------------
 // operator application
 // ---------------------------------------------------------------------------
-// block size of a stencil pass in the context's chosen variant
-static int pass_bs(const tm_ctx* c, int P, int nf, int kind) {
-    return c->variant[P][nf - 1][kind] ? STAGED_BS : DSLASH_BS;
+// blocks of a pass: one thread per site, except the direct two-flavour even pass
+// (a thread per site and flavour)
+static int pass_nblk(long vh, int nf, int kind, int staged) {
+    return staged ? nblk(vh, STAGED_BS) : nblk(nf == 2 && kind == K1_EO_INV ? 2 * vh : vh, DSLASH_BS);
 }
 
 // launch one pass in the variant the context chose for (P, NF, KIND)
@@ -343,7 +344,7 @@ static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void
                         const void* loc, SolverCtl* ctl, bool fuse, double rho = 0.0) {
     OpProb p{};
     p.g = c->g;
-    p.nblk = nblk(c->vh, pass_bs(c, P, nf, kind));
+    p.nblk = pass_nblk(c->vh, nf, kind, c->variant[P][nf - 1][kind]);
     p.bc_t = (float)c->params.bc_t;
     p.gauge[0] = gauge_ptr(c, P, 0);
     p.gauge[1] = gauge_ptr(c, P, 1);
@@ -587,14 +588,14 @@ static tm_status kernel_times_t(tm_ctx* c, int sign, const void* in, int reps, d
     CK(cudaEventCreate(&e1));
     CK(cudaEventCreate(&e2));
     b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, nullptr, false);
-    int nb = b.p[0].nblk = nblk(c->vh, v1 ? STAGED_BS : DSLASH_BS);
+    int nb = b.p[0].nblk = pass_nblk(c->vh, NF, K1_EO_INV, v1);
     b.blk_start[1] = nb;
     CK((launch_pass<P, NF, K1_EO_INV, 1>(v1, b, nb, st)));   // warm-up
     CK(cudaEventRecord(e0, st));
     for (int r = 0; r < reps; ++r) CK((launch_pass<P, NF, K1_EO_INV, 1>(v1, b, nb, st)));
     CK(cudaEventRecord(e1, st));
     b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, nullptr, false);
-    nb = b.p[0].nblk = nblk(c->vh, v2 ? STAGED_BS : DSLASH_BS);
+    nb = b.p[0].nblk = pass_nblk(c->vh, NF, K2_OE_LOCAL, v2);
     b.blk_start[1] = nb;
     for (int r = 0; r < reps; ++r) CK((launch_pass<P, NF, K2_OE_LOCAL, 1>(v2, b, nb, st)));
     CK(cudaEventRecord(e2, st));

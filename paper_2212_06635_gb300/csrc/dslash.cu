@@ -1,4 +1,5 @@
-// Even-odd Schur operator kernels of eq:hQpm (light doublet) and eq:hQh (heavy doublet).
+// Even-odd Schur operator kernels of eq:hQpm (light doublet) and the odd pass of
+// eq:hQh (heavy doublet; its even pass is in dslash_heavy.cu).
 //
 //   Q_hat psi_o = g5 [ (M_oo) psi_o - M_oe M_ee^-1 M_eo psi_o ],  M_eo = -kappa H_eo
 //
@@ -52,11 +53,11 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
 // Resident blocks the compiler must fit per SM.  Both light 16-bit passes fit in
 // 96 registers (spilling at most 16 B; the even pass streams its inverse blocks
 // two rows at a time for this), which raises occupancy from 4 to 5 blocks of
-// 128 threads.  The heavy 16-bit passes fit 4 blocks (128 registers; the even
-// pass streams its P blocks), the heavy FP32 odd pass 3 (168 registers, 8 B
-// spilled: 94.8 -> 78.1 us at 24^3x48).  The other FP32 and the FP64 passes keep
-// the default.  Sweeps at 32^3x64 (light) and 24^3x48 (heavy) put the optimum at
-// these values.
+// 128 threads.  The two-flavour odd pass fits 4 blocks in 16-bit storage (128
+// registers) and 3 in FP32 (168 registers, 8 B spilled: 94.8 -> 78.1 us at
+// 24^3x48).  The other FP32 and the FP64 passes keep the default.  Sweeps at
+// 32^3x64 (light) and 24^3x48 (heavy) put the optimum at these values.  (The
+// two-flavour even pass splits the flavours over a thread pair: dslash_heavy.cu.)
 template <int P, int NF, int KIND>
 constexpr int dslash_min_blocks() {
     if (P == PF16 || P == PB16) return NF == 1 ? 5 : 4;
@@ -65,6 +66,7 @@ constexpr int dslash_min_blocks() {
 
 template <int P, int NF, int KIND, int NP, int BS>
 __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash_kernel(const __grid_constant__ OpBatch<NP> b) {
+    static_assert(NF == 1 || KIND == K2_OE_LOCAL, "the two-flavour even pass lives in dslash_heavy.cu");
     using R = typename PT<P>::R;
     __shared__ double sh[BS / 32];
     const int k = find_problem<NP>(b, blockIdx.x);
@@ -120,74 +122,6 @@ __global__ void __launch_bounds__(BS, (dslash_min_blocks<P, NF, KIND>())) dslash
 #pragma unroll
                     for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
                 }
-            } else {
-                // heavy: [[P, E],[E, P^+]] (sign +) or [[P^+, E],[E, P]] (sign -).
-              if constexpr (P == P32) {
-                // FP32 (two resident blocks): the whole blocks are loaded at once, which
-                // keeps more loads in flight than streaming them
-                R e[72];
-                load_reals<P, 72>(pr.clov, pr.g.vh, i, 144, e);
-#pragma unroll
-                for (int cb = 0; cb < 2; ++cb) {
-                    cpx<R> vu[6], vd[6], wu[6], wd[6];
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) {
-                        vu[j] = acc[0][2 * cb + j / 3][j % 3];
-                        vd[j] = acc[NF - 1][2 * cb + j / 3][j % 3];
-                    }
-                    R m[72];
-                    load_reals<P, 72>(pr.clov, pr.g.vh, i, 72 * cb, m);
-                    if (pr.sign > 0) { full6_mv<R, false>(wu, m, vu); full6_mv<R, true>(wd, m, vd); }
-                    else { full6_mv<R, true>(wu, m, vu); full6_mv<R, false>(wd, m, vd); }
-                    herm6_mv_acc<R>(wu, e + 36 * cb, vd);
-                    herm6_mv_acc<R>(wd, e + 36 * cb, vu);
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
-                }
-              } else {
-                // 16-bit and FP64: the P block is streamed two rows (24 reals) at a time,
-                // each element serving both flavours (P v on one, P^+ v on the other); only
-                // this chirality's E block is loaded (40 reals from real 144 + 32 cb,
-                // aligned for every storage precision; the block starts 4 cb reals into
-                // them).  The 16-bit passes then fit four resident blocks.
-#pragma unroll
-                for (int cb = 0; cb < 2; ++cb) {
-                    cpx<R> vu[6], vd[6], wu[6], wd[6];
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) {
-                        vu[j] = acc[0][2 * cb + j / 3][j % 3];
-                        vd[j] = acc[NF - 1][2 * cb + j / 3][j % 3];
-                        wu[j] = C((R)0, (R)0);
-                        wd[j] = C((R)0, (R)0);
-                    }
-#pragma unroll
-                    for (int rr = 0; rr < 3; ++rr) {
-                        R m[24];
-                        load_reals<P, 24>(pr.clov, pr.g.vh, i, 72 * cb + 24 * rr, m);
-#pragma unroll
-                        for (int r2 = 0; r2 < 2; ++r2) {
-                            const int r = 2 * rr + r2;
-#pragma unroll
-                            for (int j = 0; j < 6; ++j) {
-                                const cpx<R> e = C(m[2 * (6 * r2 + j)], m[2 * (6 * r2 + j) + 1]);
-                                if (pr.sign > 0) {
-                                    cfma(wu[r], e, vu[j]);       // P v_u
-                                    cfma_cj(wd[j], e, vd[r]);    // P^+ v_d
-                                } else {
-                                    cfma_cj(wu[j], e, vu[r]);    // P^+ v_u
-                                    cfma(wd[r], e, vd[j]);       // P v_d
-                                }
-                            }
-                        }
-                    }
-                    R e40[40];
-                    load_reals<P, 40>(pr.clov, pr.g.vh, i, 144 + 32 * cb, e40);
-                    herm6_mv_acc<R>(wu, e40 + 4 * cb, vd);
-                    herm6_mv_acc<R>(wd, e40 + 4 * cb, vu);
-#pragma unroll
-                    for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
-                }
-              }
             }
         } else {
             // out = g5 [ (A + i tw g5 [tau3]) psi - eps tau1 psi - kappa^2 acc ]
@@ -246,8 +180,8 @@ cudaError_t launch_dslash(const OpBatch<NP>& b, int nblocks, cudaStream_t st) {
 #define TM_INST(P, NF, KIND, NP) \
     template cudaError_t launch_dslash<P, NF, KIND, NP>(const OpBatch<NP>&, int, cudaStream_t);
 #define TM_INST_P(P)                                                                      \
-    TM_INST(P, 1, K1_EO_INV, 1) TM_INST(P, 1, K2_OE_LOCAL, 1) TM_INST(P, 2, K1_EO_INV, 1) \
-    TM_INST(P, 2, K2_OE_LOCAL, 1) TM_INST(P, 1, K1_EO_INV, MAXP) TM_INST(P, 1, K2_OE_LOCAL, MAXP)
+    TM_INST(P, 1, K1_EO_INV, 1) TM_INST(P, 1, K2_OE_LOCAL, 1) TM_INST(P, 2, K2_OE_LOCAL, 1) \
+    TM_INST(P, 1, K1_EO_INV, MAXP) TM_INST(P, 1, K2_OE_LOCAL, MAXP)
 TM_INST_P(P64)
 TM_INST_P(P32)
 TM_INST_P(PB16)

@@ -263,24 +263,38 @@ __global__ void __launch_bounds__(BS) dslash_staged_kernel(const __grid_constant
                     for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
                 }
             } else {
-                R e[72];
-                reals_from_smem<P, 72>(s16, ue + 144 * G::ESZ / 16, BS, t, e);
+                // heavy: per chirality [A_c - 1 36][D_c - 1 36] (the layout and the
+                // block inverse are described in dslash_heavy.cu):
+                //   w_u = A D v_u - i s sigma mubar_t D v_u + epsbar_t D v_d, and u <-> d with +i
+                const R tw = (R)pr.tw, eps = (R)pr.eps;
 #pragma unroll
                 for (int cb = 0; cb < 2; ++cb) {
-                    cpx<R> vu[6], vd[6], wu[6], wd[6];
+                    cpx<R> vu[6], vd[6], du[6], dd[6], wu[6], wd[6];
 #pragma unroll
                     for (int j = 0; j < 6; ++j) {
                         vu[j] = acc[0][2 * cb + j / 3][j % 3];
                         vd[j] = acc[NF - 1][2 * cb + j / 3][j % 3];
+                        du[j] = vu[j];
+                        dd[j] = vd[j];
                     }
-                    R m[72];
-                    reals_from_smem<P, 72>(s16, ue + 72 * cb * G::ESZ / 16, BS, t, m);
-                    if (pr.sign > 0) { full6_mv<R, false>(wu, m, vu); full6_mv<R, true>(wd, m, vd); }
-                    else { full6_mv<R, true>(wu, m, vu); full6_mv<R, false>(wd, m, vd); }
-                    herm6_mv_acc<R>(wu, e + 36 * cb, vd);
-                    herm6_mv_acc<R>(wd, e + 36 * cb, vu);
+                    R m[40];
+                    reals_from_smem<P, 40>(s16, ue + (72 * cb + 32) * G::ESZ / 16, BS, t, m);   // D_c - 1 at m + 4
+                    herm6_mv_acc<R>(du, m + 4, vu);
+                    herm6_mv_acc<R>(dd, m + 4, vd);
 #pragma unroll
-                    for (int j = 0; j < 6; ++j) { out[6 * cb + j] = wu[j]; out[12 + 6 * cb + j] = wd[j]; }
+                    for (int j = 0; j < 6; ++j) {
+                        wu[j] = du[j];
+                        wd[j] = dd[j];
+                    }
+                    reals_from_smem<P, 40>(s16, ue + 72 * cb * G::ESZ / 16, BS, t, m);          // A_c - 1 at m
+                    herm6_mv_acc<R>(wu, m, du);
+                    herm6_mv_acc<R>(wd, m, dd);
+                    const R ts = cb == 0 ? tw : -tw;
+#pragma unroll
+                    for (int j = 0; j < 6; ++j) {
+                        out[6 * cb + j] = wu[j] - ts * mul_i(du[j]) + eps * dd[j];
+                        out[12 + 6 * cb + j] = wd[j] + ts * mul_i(dd[j]) + eps * du[j];
+                    }
                 }
             }
         } else {

@@ -202,7 +202,7 @@ __device__ __forceinline__ void put_real(double* base, long vh, long i, int r, d
 //   a1 = F_yz + s F_xt,  a2 = -F_xz + s F_yt,  a3 = F_xy + s F_zt  (s = +1 / -1 per chirality),
 // which is the chirality-block form of 1 - kappa csw sum_{mu<nu} g_mu g_nu F_munu.
 // Writes A (packed hermitian, 72 reals/site); on even sites also the light inverse
-// blocks B_c = (A_c + i s mu_t)^-1 (144 reals) and/or the heavy blocks P_c, E_c (216).
+// blocks B_c = (A_c + i s mu_t)^-1 (144 reals) and/or the heavy A_c, D_c (144).
 __global__ void k_clover(Geom g, const void* g0, const void* g1, int par, double kappa, double csw,
                          double mu_t, double mubar_t, double epsbar_t, double* outA,
                          double* outB, double* outH) {
@@ -271,23 +271,18 @@ __global__ void k_clover(Geom g, const void* g0, const void* g1, int par, double
             for (int k = 0; k < 36; ++k) D[k] = A2[k];
             for (int r = 0; r < 6; ++r) D[7 * r].re += mubar_t * mubar_t - epsbar_t * epsbar_t;
             hpd6_inverse(D);
-            for (int r = 0; r < 6; ++r)
-                for (int j = 0; j < 6; ++j) {
-                    cd t = C(0.0, 0.0);
-                    for (int k = 0; k < 6; ++k) {
-                        cd a = A[6 * r + k];
-                        if (k == r) a.im -= s * mubar_t;
-                        cfma(t, a, D[6 * k + j]);
-                    }
-                    put_real(outH, g.vh, i, 72 * cb + 2 * (6 * r + j), t.re);
-                    put_real(outH, g.vh, i, 72 * cb + 2 * (6 * r + j) + 1, t.im);
-                }
-            // E = epsbar_t D (hermitian, packed)
-            for (int r = 0; r < 6; ++r) put_real(outH, g.vh, i, 144 + 36 * cb + r, epsbar_t * D[7 * r].re);
+            // [A_c - 1 36][D_c - 1 36] per chirality, both packed hermitian (the
+            // deviation from the identity keeps 16-bit rounding relative to it)
+            for (int r = 0; r < 6; ++r) {
+                put_real(outH, g.vh, i, 72 * cb + r, A[7 * r].re - 1.0);
+                put_real(outH, g.vh, i, 72 * cb + 36 + r, D[7 * r].re - 1.0);
+            }
             for (int r = 1; r < 6; ++r)
                 for (int j = 0; j < r; ++j) {
-                    put_real(outH, g.vh, i, 144 + 36 * cb + herm_off(r, j), epsbar_t * D[6 * r + j].re);
-                    put_real(outH, g.vh, i, 144 + 36 * cb + herm_off(r, j) + 1, epsbar_t * D[6 * r + j].im);
+                    put_real(outH, g.vh, i, 72 * cb + herm_off(r, j), A[6 * r + j].re);
+                    put_real(outH, g.vh, i, 72 * cb + herm_off(r, j) + 1, A[6 * r + j].im);
+                    put_real(outH, g.vh, i, 72 * cb + 36 + herm_off(r, j), D[6 * r + j].re);
+                    put_real(outH, g.vh, i, 72 * cb + 36 + herm_off(r, j) + 1, D[6 * r + j].im);
                 }
         }
     }

@@ -256,14 +256,15 @@ __device__ __forceinline__ void load_link(const void* base, long vh, int mu, lon
 //   full 6x6 block: row major complex: 72 reals.
 //   odd  A:       [A0 herm 36][A1 herm 36]                          72 reals
 //   even light:   [B0 full 72][B1 full 72]  B_c = (A_c + i s_c mu_t)^-1   144 reals
-//   even heavy:   [P0 72][P1 72][E0 36][E1 36]                    216 reals
-//                 P_c = (A_c - i s_c mubar_t) D_c,  E_c = epsbar_t D_c,
-//                 D_c = (A_c^2 + mubar_t^2 - epsbar_t^2)^-1
+//   even heavy:   [A0-1 herm 36][D0-1 herm 36][A1-1 herm 36][D1-1 herm 36]  144 reals
+//                 D_c = (A_c^2 + mubar_t^2 - epsbar_t^2)^-1; the block inverse
+//                 [[(A_c - i s_c mubar_t) D_c, epsbar_t D_c], [epsbar_t D_c, (A_c + i s_c mubar_t) D_c]]
+//                 is applied from A_c and D_c (they commute)
 // (s_c = +1 for chirality 0 = spins 0,1 and -1 for spins 2,3.)
 // ---------------------------------------------------------------------------
 constexpr int CLOV_ODD_REALS = 72;
 constexpr int CLOV_EVEN_LIGHT_REALS = 144;
-constexpr int CLOV_EVEN_HEAVY_REALS = 216;
+constexpr int CLOV_EVEN_HEAVY_REALS = 144;
 
 __host__ __device__ constexpr int herm_off(int i, int j) {   // i > j
     return 6 + 2 * (i * (i - 1) / 2 + j);
