@@ -453,6 +453,12 @@ tm_status tm_autotune(tm_ctx* ctx, tm_prec prec, int nflavour, tm_tuning* chosen
 tm_status tm_set_tuning(tm_ctx* ctx, tm_prec prec, int nflavour, const tm_tuning* tuning);
 tm_status tm_get_tuning(const tm_ctx* ctx, tm_prec prec, int nflavour, tm_tuning* tuning);
 
+/* Measured fused multiply-add rate of the CUDA cores in FP64 or FP32 (flops per
+ * second, 2 per FMA): register-resident chains on every SM, CUDA-event timed.
+ * The roofline denominator of passes bound by arithmetic instead of memory; the
+ * paper has no counterpart.  Synchronous; allocates a few bytes. */
+tm_status tm_fma_rate(int device, tm_prec prec, double* flops_per_s);
+
 /* Message of the calling thread's last failure ("" if none). */
 const char* tm_last_error(void);
 

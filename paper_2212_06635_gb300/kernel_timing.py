@@ -10,6 +10,9 @@ here, and the ncu captures under profiles/ run these same launch sequences.
   ... --ptc-grad                  loss and gradient of that network, 1 + reps times
   ... --ptc-fcg ITERS             ITERS iterations of PTC-preconditioned flexible CG
   ... --solve                     one mixed-precision CG solve (--prec storage) to 1e-10
+  ... --multishift                a 12-shift heavy-doublet multishift solve (--prec storage)
+  ... --mg ITERS                  multigrid setup and ITERS multigrid-preconditioned GCR iterations
+  ... --fma                       measured FP64 and FP32 FMA rates of the CUDA cores
 """
 from __future__ import annotations
 
@@ -233,6 +236,62 @@ def cg_solve(dims, prec, quiet=False):
         tm.tm_destroy(ctx)
 
 
+def multishift(dims, prec, nshift=12, quiet=False):
+    """One heavy-doublet multishift solve (Q_h Q_h^dag, nshift shifts log-spaced in
+    [1e-5, 1] x 1.02 lambda_max) in storage prec, refined shift by shift to 1e-10:
+    the launch sequence of the multishift update kernels."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    ctx = _ctx(tm, dims, True, seed=1002)
+    try:
+        if prec != 0:
+            tm.tm_autotune(ctx, prec, 2)
+        lam = 1.02 * tm.tm_power_iteration(ctx, tm.TM_QH_SQ, 50)
+        shifts = [lam * 10.0 ** (-5 + 5 * k / (nshift - 1)) for k in range(nshift)]
+        bd = torch.from_numpy(F.odd_spinor(dims, 2002, 2).view(np.float64).copy()).cuda()
+        xs = [torch.zeros_like(bd) for _ in shifts]
+        infos = tm.tm_solve_multishift(ctx, tm.TM_QH_SQ, shifts, xs, bd, tm.solve_params(tol=1e-10, sloppy=prec),
+                                       check=False)
+        if not quiet:
+            print(f"dims {dims} multishift {nshift} shifts, storage {prec}: {infos[0].seconds:.4f} s, "
+                  f"iterations {[i.iters for i in infos]}")
+        return infos
+    finally:
+        tm.tm_destroy(ctx)
+
+
+def mg_solve(dims, block=(4, 4, 4, 4), nvec=12, setup=100, smooth=8, maxiter=20, quiet=False):
+    """Multigrid setup (FP32) and a bounded multigrid-preconditioned GCR solve of
+    the full operator: the launch sequence of the multigrid kernels."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    ctx = _ctx(tm, dims, False, seed=1004)
+    mg = None
+    try:
+        V = int(np.prod(dims))
+        g = torch.Generator(device="cuda")
+        g.manual_seed(7)
+        init = torch.randn(nvec * V * 24, dtype=torch.float64, device="cuda", generator=g)
+        b = torch.randn(V * 24, dtype=torch.float64, device="cuda", generator=g)
+        mg = tm.tm_mg_create(ctx, tm.mg_params(block, nvec, setup, smooth, 1, tm.TM_F32, 0.1, 30, 16))
+        t0 = time.perf_counter()
+        tm.tm_mg_setup(mg, init)
+        ts = time.perf_counter() - t0
+        del init
+        x = torch.zeros_like(b)
+        info = tm.tm_solve_gcr(ctx, 1, mg, tm.solve_params(tol=1e-10, maxiter=maxiter, sloppy=tm.TM_F32, chunk=16),
+                               x, b, check=False)
+        if not quiet:
+            print(f"dims {dims} multigrid setup {ts:.3f} s; GCR {info.iters} iterations {info.seconds:.3f} s "
+                  f"residual {info.true_rel_res:.2e}")
+        return info
+    finally:
+        if mg is not None:
+            tm.tm_mg_destroy(mg)
+        tm.tm_destroy(ctx)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
@@ -246,6 +305,11 @@ def main():
     ap.add_argument("--ptc-grad", action="store_true")
     ap.add_argument("--force", type=int, default=0, metavar="NPAIRS")
     ap.add_argument("--solve", action="store_true")
+    ap.add_argument("--multishift", action="store_true")
+    ap.add_argument("--mg", type=int, default=0, metavar="ITERS",
+                    help="multigrid setup, then ITERS iterations of multigrid-preconditioned GCR")
+    ap.add_argument("--setup", type=int, default=100, help="--mg: minimal-residual steps per near-null vector")
+    ap.add_argument("--fma", action="store_true", help="measured FP64 and FP32 FMA rates")
     a = ap.parse_args()
     dims = tuple(a.dims)
     prec = PRECS[a.prec]
@@ -260,6 +324,14 @@ def main():
         force_outer(dims, prec, nf, a.force, a.reps)
     elif a.solve:
         cg_solve(dims, prec)
+    elif a.multishift:
+        multishift(dims, prec)
+    elif a.mg:
+        mg_solve(dims, setup=a.setup, maxiter=a.mg)
+    elif a.fma:
+        from paper_2212_06635_gb300 import tm
+        for p, name in ((0, "FP64"), (1, "FP32")):
+            print(f"{name} FMA rate: {tm.tm_fma_rate(0, p) / 1e12:.3f} TFLOP/s")
     else:
         stencil_passes(dims, prec, nf, a.reps, a.variant)
 

@@ -116,6 +116,7 @@ _sigs = {
     "tm_ptc_load": [_vp, ct.c_char_p],
     "tm_solve_fcg": [_vp, ct.c_int, _vp, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
     "tm_apply_full": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_fma_rate": [ct.c_int, ct.c_int, ct.POINTER(ct.c_double)],
     "tm_mg_create": [ct.POINTER(_vp), _vp, ct.POINTER(tm_mg_params)],
     "tm_mg_destroy": [_vp],
     "tm_mg_coarse_size": [_vp, ct.POINTER(ct.c_size_t)],
@@ -506,3 +507,10 @@ def tm_solve_gcr(ctx, sign, mg, sp, x, b, stream=None, check=True):
     if check:
         _check(st)
     return info
+
+
+def tm_fma_rate(device, prec):
+    """Measured FMA rate of the CUDA cores, flops per second (FP64 or FP32)."""
+    v = ct.c_double()
+    _check(lib.tm_fma_rate(int(device), int(prec), ct.byref(v)))
+    return v.value
