@@ -13,7 +13,16 @@ same JSON line carries the second half of the metric: seconds to true relative
 residual 1e-10 of the chosen form (mixed-precision CG) and of plain FP64 CG on
 the same GPU.
 
+Before that headline line, one JSON line holds the records of the other
+workloads: the heavy-doublet multishift at 24^3x48, the uneven batch, the force
+outer products, the rational correction term, the two-level multigrid of the
+full operator at 48^3x96 against the even-odd mixed CG route, and the PTC
+network trained on 2048 solver-generated pairs from 8 configurations at
+48^3x96 inside flexible CG.  The headline line repeats their times to solution
+under `workload_summary`.
+
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
+                  [--no-extra] [--no-mg] [--no-ptc] [--ptc-quick]
 """
 from __future__ import annotations
 
@@ -435,6 +444,11 @@ def run_ours(args, rank, world, local_rank):
         extra["batch_uneven_24"] = run_batch(tm, args)
         extra["force_outer_heavy_24x48"] = run_force(args, peak)
         extra["rational_correction_heavy_24x48"] = run_rational(tm, args)
+    if rank == 0 and not args.no_mg:
+        try:
+            extra["mg_gcr_48x96"] = run_mg(tm, args)
+        except Exception as e:  # recorded in the line, not swallowed
+            extra["mg_gcr_48x96"] = {"error": repr(e)}
     if rank == 0 and not args.no_ptc:
         try:
             extra["ptc_fcg_48x96"] = run_ptc(tm, args)
@@ -504,8 +518,11 @@ def summarize(extra):
     elif "error" in pt:
         out["ptc_48x96"] = {"error": pt["error"][:200]}
     mg = extra.get("mg_gcr_48x96", {})
-    if mg:
-        out["mg_48x96"] = {k: v for k, v in mg.items() if k.endswith("_s") or k.endswith("_iters")}
+    if "mg_gcr_s" in mg:
+        out["mg_48x96"] = {k: mg[k] for k in ("mg_setup_s", "mg_gcr_s", "mg_gcr_iters", "eo_mixed_cg_s",
+                                              "speedup_mg_vs_eo_mixed_cg") if k in mg}
+    elif "error" in mg:
+        out["mg_48x96"] = {"error": mg["error"][:200]}
     return out
 
 
@@ -656,6 +673,112 @@ def run_rational(tm, args):
     return out
 
 
+def _parity_lex(dims, parity, dev):
+    """Lexicographic index of every site of one parity, in the half-lattice order
+    of the native fields (site k of that parity has lex // 2 == k)."""
+    import torch
+    X, Y, Z, T = dims
+    lex0 = 2 * torch.arange(X * Y * Z * T // 2, device=dev, dtype=torch.int64)
+    r = lex0 // X
+    yzt = (r % Y) + ((r // Y) % Z) + (r // (Y * Z))
+    return lex0 + ((yzt + parity) % 2)     # x = lex % X: even at lex0, so x parity is the offset
+
+
+def run_mg(tm, args):
+    """48^3x96 (the PTC workload's action): the full system M x = b, b on odd
+    sites, to FP64 true relative residual 1e-10 by (a) multigrid-preconditioned
+    GCR (Sec. 4.1's method; FP32 hierarchy and inner GCR, FP64 defect correction)
+    and (b) the even-odd route of mixed-precision CG: M_hat^dag M_hat y = M_hat^dag b_o
+    in FP16 storage, x_o = y, x_e = kappa M_ee^-1 H_eo y.  Both solutions are
+    checked by the FP64 full residual; CG's normal-equation tolerance is tightened
+    until that residual reaches 1e-10.  Multigrid setup time is reported apart."""
+    import torch
+    w = CFG.PTC_48
+    V = w.volume
+    vh = V // 2
+    p = CFG.MG_PARAMS
+    dev = torch.device("cuda")
+    out = {"workload": "full system M x = b at 48^3x96, b on odd sites", "lattice": list(w.dims),
+           "mg": {k: (list(v) if isinstance(v, tuple) else v) for k, v in p.items()}}
+    ctx = tm.tm_create(w.dims, 0)
+    mg = None
+    try:
+        tm.tm_gauge_load(ctx, F.gauge_field(w.dims, w.link_seed), 1.0)
+        tm.tm_clover_compute(ctx, w.kappa, w.csw, mu=w.mu, bc_t=w.bc_t)
+        tm.tm_autotune(ctx, tm.TM_F16, 1)
+        bod = torch.from_numpy(F.odd_spinor(w.dims, w.rhs_seed).view(np.float64).copy()).to(dev)
+        lex_o = _parity_lex(w.dims, 1, dev)
+        lex_e = _parity_lex(w.dims, 0, dev)
+        bfull = torch.zeros(V, 24, dtype=torch.float64, device=dev)
+        bfull[lex_o] = bod.view(vh, 24)
+        bfull = bfull.view(-1)
+        bn = float(torch.linalg.vector_norm(bfull))
+
+        def full_res(x):
+            r = torch.empty_like(bfull)
+            tm.tm_apply_full(ctx, 1, tm.TM_F64, r, x)
+            torch.cuda.synchronize()
+            return float(torch.linalg.vector_norm(bfull - r)) / bn
+
+        # (a) multigrid-preconditioned GCR
+        g = torch.Generator(device=dev)
+        g.manual_seed(6000)
+        init = torch.randn(p["nvec"] * V * 24, dtype=torch.float64, device=dev, generator=g)
+        mg = tm.tm_mg_create(ctx, tm.mg_params(p["block"], p["nvec"], p["setup_steps"], p["smooth_steps"], 1,
+                                               tm.TM_F32, p["coarse_tol"], p["coarse_maxiter"], p["coarse_restart"]))
+        _sync()
+        t0 = time.perf_counter()
+        tm.tm_mg_setup(mg, init)
+        _sync()
+        out["mg_setup_s"] = round(time.perf_counter() - t0, 3)
+        del init
+        x = torch.zeros_like(bfull)
+        info = tm.tm_solve_gcr(ctx, 1, mg, tm.solve_params(tol=w.tol, maxiter=p["maxiter"], sloppy=tm.TM_F32,
+                                                           chunk=p["restart"]), x, bfull, check=False)
+        out["mg_gcr"] = info.as_dict()
+        out["mg_gcr_s"] = round(info.seconds, 3)
+        out["mg_gcr_iters"] = info.iters
+        out["mg_gcr_full_res"] = full_res(x)
+        tm.tm_mg_destroy(mg)
+        mg = None
+        # (b) even-odd mixed CG on the normal equations
+        g5b = bod.view(vh, 4, 6).clone()
+        g5b[:, 2:, :] *= -1.0
+        nb64 = tm.tm_field_bytes(ctx, tm.TM_F64, 1)
+        fa = torch.empty(nb64, dtype=torch.uint8, device=dev)
+        fb = torch.empty(nb64, dtype=torch.uint8, device=dev)
+        c = torch.empty_like(bod)
+        tm.tm_field_import(ctx, tm.TM_F64, 1, fa, g5b.view(-1))
+        tm.tm_apply_Mhat(ctx, tm.TM_QHAT_MINUS, tm.TM_F64, fb, fa)     # M_hat^dag b_o = Q_hat_- g5 b_o
+        tm.tm_field_export(ctx, tm.TM_F64, 1, c, fb)
+        y = torch.zeros_like(bod)
+        xe = torch.empty_like(bod)
+        for tol in (1e-10, 1e-11, 1e-12):
+            y.zero_()
+            inf = tm.tm_solve_cg(ctx, tm.TM_MDAGM, tm.solve_params(tol=tol, sloppy=tm.TM_F16), y, c, check=False)
+            t0 = time.perf_counter()
+            tm.tm_field_import(ctx, tm.TM_F64, 1, fa, y)
+            tm.tm_apply_even(ctx, tm.TM_QHAT_PLUS, tm.TM_F64, fb, fa)
+            tm.tm_field_export(ctx, tm.TM_F64, 1, xe, fb)
+            xf = torch.empty(V, 24, dtype=torch.float64, device=dev)
+            xf[lex_o] = y.view(vh, 24)
+            xf[lex_e] = w.kappa * xe.view(vh, 24)
+            _sync()
+            recon = time.perf_counter() - t0
+            res = full_res(xf.view(-1))
+            out["eo_mixed_cg"] = {"normal_tol": tol, "iters": inf.iters, "seconds": round(inf.seconds + recon, 3),
+                                  "full_res": res, "status": tm.STATUS_NAMES[inf.status]}
+            if res <= w.tol:
+                break
+        out["eo_mixed_cg_s"] = out["eo_mixed_cg"]["seconds"]
+        out["speedup_mg_vs_eo_mixed_cg"] = round(out["eo_mixed_cg_s"] / max(out["mg_gcr_s"], 1e-9), 3)
+    finally:
+        if mg is not None:
+            tm.tm_mg_destroy(mg)
+        tm.tm_destroy(ctx)
+    return out
+
+
 def run_ptc(tm, args):
     """48^3x96: train the 4-layer 8-channel PTC network on solver-generated pairs
     from several seeded configurations, then solve on the benchmark configuration
@@ -731,6 +854,7 @@ def main():
                     help="skip the heavy multishift and uneven batch workloads")
     ap.add_argument("--no-ptc", action="store_true",
                     help="skip the PTC training + PTC-FCG workload on 48^3x96")
+    ap.add_argument("--no-mg", action="store_true", help="skip the multigrid workload on 48^3x96")
     ap.add_argument("--ptc-quick", action="store_true",
                     help="short PTC training (512 pairs from 2 configurations) instead of the workload's "
                          "2048 pairs from 8 configurations")

@@ -1619,10 +1619,13 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
     while (remaining > 0) {
         if (gexec) CK(cudaGraphLaunch(gexec, st));
         else for (int it = 0; it < chunk; ++it) CK(iteration());
+        // every running problem's control word in one synchronisation
+        for (int q = 0; q < n; ++q)
+            if (!done[q]) CK(cudaMemcpyAsync(cs[q]->h_ctl, cs[q]->ctl, sizeof(SolverCtl), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
         for (int q = 0; q < n; ++q) {
             if (done[q]) continue;
             tm_ctx* c = cs[q];
-            CKS(get_ctl(c, st));
             SolverCtl& h = *c->h_ctl;
             if (h.flag == CTL_RUN) continue;
             infos[q].iters = h.iter;

@@ -16,7 +16,8 @@
 //                  Gram-Schmidt applied twice); stored [a][j][spin2 colour3][site]
 //                  so that a warp's loads of one column are contiguous;
 //   coarse op.     M_c = P^+ M P, nearest neighbour on the block lattice: per block
-//                  9 dense (2 nvec)^2 complex blocks (self, +x, -x, ..., -t) built
+//                  9 dense (2 nvec)^2 complex blocks (self, +x, -x, ..., -t), stored
+//                  column-major so that the rows of a column are contiguous, built
 //                  directly (CUDA block per (block, source column): the column's
 //                  fine image under the local term and every hop, split by the
 //                  block the hop starts from, dotted with the block's columns);
@@ -65,7 +66,7 @@ namespace tmk {
 constexpr int MG_MAX_NVEC = 16;
 constexpr int MG_MAX_RESTART = 16;
 constexpr int MG_BS = 256;
-constexpr int MG_GRID_CAP = 1216;        // 8 blocks on each of 152 SMs: grid of every flat-vector kernel
+constexpr int MG_GRID_CAP = 608;         // 4 blocks of 256 on each of 152 SMs: grid of every flat-vector kernel
 constexpr int MG_NSLOT = 9;              // self, +x, -x, +y, -y, +z, -z, +t, -t
 constexpr int MG_NDOT = MG_MAX_RESTART + 1;
 constexpr int MG_PART_W = 2 * MG_NDOT;   // doubles per block partial
@@ -232,12 +233,16 @@ __global__ void __launch_bounds__(MG_BS) k_pairdots(const __grid_constant__ Pair
     __syncthreads();
     if (!am_last) return;
     __threadfence();
-    if (threadIdx.x < 2 * a.np) {
-        double t = 0.0;
-        for (int b = 0; b < (int)gridDim.x; ++b) t += ((volatile double*)a.partial)[(long)b * MG_PART_W + threadIdx.x];
-        tot[threadIdx.x] = t;
+    // every thread sums a fixed stride of the block partials, then one block sum:
+    // the same order for a given grid
+#pragma unroll
+    for (int q = 0; q < 2 * NP; ++q) acc[q] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += MG_BS) {
+#pragma unroll
+        for (int q = 0; q < 2 * NP; ++q)
+            if (q < 2 * a.np) acc[q] += ((volatile double*)a.partial)[(long)b * MG_PART_W + q];
     }
-    __syncthreads();
+    block_sums<2 * NP>(acc, red, tot);
     if (threadIdx.x == 0) {
         *a.counter = 0u;
         mg_finalize(a.fin, tot, a.np, a.ctl);
@@ -381,13 +386,15 @@ __global__ void __launch_bounds__(MG_BS) k_gcr_update(long n, void* z, void* az,
     __syncthreads();
     if (threadIdx.x == 0) am_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
     __syncthreads();
-    if (!am_last || threadIdx.x != 0) return;
+    if (!am_last) return;
     __threadfence();
-    double t = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) t += ((volatile double*)partial)[(long)b * MG_PART_W];
-    *counter = 0u;
-    const double tt[1] = {t};
-    mg_finalize(MGF_RR, tt, 1, ctl);
+    acc[0] = 0.0;
+    for (int b = threadIdx.x; b < (int)gridDim.x; b += MG_BS) acc[0] += ((volatile double*)partial)[(long)b * MG_PART_W];
+    block_sums<1>(acc, red, tot);
+    if (threadIdx.x == 0) {
+        *counter = 0u;
+        mg_finalize(MGF_RR, tot, 1, ctl);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -404,6 +411,9 @@ struct FullOp {
     void* out;
     size_t half;             // bytes of one parity half of a full field
     const MgCtl* gate;       // early exit when gate->flag != CTL_RUN (may be null)
+    MgCtl* mr;               // non-null: fuse the minimal-residual dots <out, in>, <out, out> (MGF_MR)
+    double* partial;         // per-block partials of the fused dots (3 per block)
+    unsigned int* counter;
 };
 
 template <int P, int MU>
@@ -433,13 +443,43 @@ __device__ __forceinline__ void full_hop(cpx<typename PT<P>::R> (&acc)[4][3], co
     hop_dir<R, MU, +1, true>(acc, psi, u, ph_b);
 }
 
-// out(x) = A(x) psi(x) + i tw g5 psi(x) - kappa (H psi)(x), one thread per site of either parity
+template <int P>
+__device__ __forceinline__ void full_op_site(const FullOp& a, long gi, double (&d)[3]);
+
+// out(x) = A(x) psi(x) + i tw g5 psi(x) - kappa (H psi)(x), one thread per site of
+// either parity; optionally the minimal-residual step's dots of (out, psi) fused
 template <int P>
 __global__ void __launch_bounds__(128) k_full_op(const __grid_constant__ FullOp a) {
-    using R = typename PT<P>::R;
     if (a.gate && a.gate->flag != CTL_RUN) return;
     const long gi = (long)blockIdx.x * 128 + threadIdx.x;
-    if (gi >= 2 * a.g.vh) return;
+    double d[3] = {0.0, 0.0, 0.0};
+    if (gi < 2 * a.g.vh) full_op_site<P>(a, gi, d);
+    if (!a.mr) return;
+    __shared__ double red[(128 / 32) * 3];
+    __shared__ double tot[3];
+    block_sums<3>(d, red, tot);
+    __shared__ int am_last;
+    if (threadIdx.x < 3) a.partial[(long)blockIdx.x * 3 + threadIdx.x] = tot[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) am_last = (atomicAdd(a.counter, 1u) == gridDim.x - 1);
+    __syncthreads();
+    if (!am_last) return;
+    __threadfence();
+    d[0] = d[1] = d[2] = 0.0;
+    for (long b = threadIdx.x; b < (long)gridDim.x; b += 128)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) d[q] += ((volatile double*)a.partial)[b * 3 + q];
+    block_sums<3>(d, red, tot);
+    if (threadIdx.x == 0) {
+        *a.counter = 0u;
+        mg_finalize(MGF_MR, tot, 2, a.mr);
+    }
+}
+
+template <int P>
+__device__ __forceinline__ void full_op_site(const FullOp& a, long gi, double (&d)[3]) {
+    using R = typename PT<P>::R;
     const int po = gi >= a.g.vh ? 1 : 0;
     const long i = gi - po * a.g.vh;
     const Coord c = cb_coords(a.g, i, po);
@@ -472,6 +512,18 @@ __global__ void __launch_bounds__(128) k_full_op(const __grid_constant__ FullOp 
         for (int j = 0; j < 6; ++j) out[6 * cb + j] = w[j];
     }
     store_spinor<P, 12>(reinterpret_cast<char*>(a.out) + (size_t)po * a.half, a.g.vh, i, out);
+    if (a.mr) {
+        R t0 = (R)0, t1 = (R)0, t2 = (R)0;
+#pragma unroll
+        for (int q = 0; q < 12; ++q) {
+            t0 += out[q].re * psi[q].re + out[q].im * psi[q].im;
+            t1 += out[q].re * psi[q].im - out[q].im * psi[q].re;
+            t2 += norm2(out[q]);
+        }
+        d[0] = (double)t0;
+        d[1] = (double)t1;
+        d[2] = (double)t2;
+    }
 }
 
 // canonical full field [lex][spin][colour] (FP64) <-> native full field
@@ -632,43 +684,46 @@ __global__ void __launch_bounds__(MG_BS) k_mg_orth(void* Pm, MgGeom m) {
     }
 }
 
-// coarse = P^+ fine: one CUDA block per lattice block k, rows r = h nvec + j
+// coarse = P^+ fine: one CUDA block per lattice block k, rows r = h nvec + j,
+// one chirality at a time (a thread holds the nvec sums of one chirality)
 template <int P, int NV>
-__global__ void __launch_bounds__(MG_BS) k_mg_restrict(void* coarse, const void* fine, const void* Pm, MgGeom m,
-                                                        const MgCtl* gate) {
+__global__ void __launch_bounds__(MG_BS, 2) k_mg_restrict(void* coarse, const void* fine, const void* Pm, MgGeom m,
+                                                           const MgCtl* gate) {
     using R = typename PT<P>::R;
     if (gate && gate->flag != CTL_RUN) return;
     const int k = blockIdx.x;
     const int nv = m.nvec;
-    double acc[4 * NV];
+    __shared__ double red[(MG_BS / 32) * 2 * NV];
+    __shared__ double tot[2 * NV];
+    for (int h = 0; h < 2; ++h) {
+        R accr[2 * NV];   // per-thread sums (a thread covers Vb / blockDim sites) in the arithmetic precision
 #pragma unroll
-    for (int q = 0; q < 4 * NV; ++q) acc[q] = 0.0;
-    for (int s = threadIdx.x; s < m.Vb; s += blockDim.x) {
-        int x[4];
-        block_site(m, k, s, x);
-        const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-        cpx<R> v[12];
-        load_spinor<P, 12>(reinterpret_cast<const char*>(fine) + (size_t)par * m.half, m.g.vh, lex_of(m.g, x) >> 1, v);
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int q = 0; q < 2 * NV; ++q) accr[q] = (R)0;
+        for (int s = threadIdx.x; s < m.Vb; s += blockDim.x) {
+            int x[4];
+            block_site(m, k, s, x);
+            const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
+            cpx<R> v[6];   // spins 2h, 2h+1 (reals 12 h .. 12 h + 11)
+            load_reals<P, 12>(reinterpret_cast<const char*>(fine) + (size_t)par * m.half, m.g.vh, lex_of(m.g, x) >> 1,
+                              12 * h, reinterpret_cast<R*>(v));
 #pragma unroll
             for (int j = 0; j < NV; ++j) {
                 if (j < nv) {
                     cpx<R> t = C((R)0, (R)0);
 #pragma unroll
-                    for (int c = 0; c < 6; ++c) cfma_cj(t, ldc<P>(Pm, p_index(m, 2 * k + h, j, c, s)), v[6 * h + c]);
-                    acc[2 * (h * NV + j)] += (double)t.re;
-                    acc[2 * (h * NV + j) + 1] += (double)t.im;
+                    for (int c = 0; c < 6; ++c) cfma_cj(t, ldc<P>(Pm, p_index(m, 2 * k + h, j, c, s)), v[c]);
+                    accr[2 * j] += t.re;
+                    accr[2 * j + 1] += t.im;
                 }
             }
-    }
-    __shared__ double red[(MG_BS / 32) * 4 * NV];
-    __shared__ double tot[4 * NV];
-    block_sums<4 * NV>(acc, red, tot);
-    if (threadIdx.x < 2 * nv) {
-        const int h = threadIdx.x / nv, j = threadIdx.x % nv;
-        stc<P>(coarse, (long)k * 2 * nv + threadIdx.x,
-               C((typename CE<P>::R)tot[2 * (h * NV + j)], (typename CE<P>::R)tot[2 * (h * NV + j) + 1]));
+        }
+        double acc[2 * NV];
+#pragma unroll
+        for (int q = 0; q < 2 * NV; ++q) acc[q] = (double)accr[q];
+        block_sums<2 * NV>(acc, red, tot);
+        if (threadIdx.x < nv)
+            stc<P>(coarse, (long)k * 2 * nv + h * nv + threadIdx.x,
+                   C((typename CE<P>::R)tot[2 * threadIdx.x], (typename CE<P>::R)tot[2 * threadIdx.x + 1]));
     }
 }
 
@@ -696,7 +751,8 @@ __global__ void __launch_bounds__(MG_BS) k_mg_prolong(void* fine, const void* co
     store_spinor<P, 12>(reinterpret_cast<char*>(fine) + (size_t)par * m.half, m.g.vh, lex_of(m.g, x) >> 1, v);
 }
 
-// out = M_c in: one thread per (block k, row r); M_c stored [k][slot][r][c]
+// out = M_c in: one thread per (block k, row r); M_c stored [k][slot][c][r], so
+// that a warp's loads of one column are contiguous
 template <int P>
 __global__ void __launch_bounds__(MG_BS) k_mg_coarse(void* out, const void* in, const void* Mc, MgGeom m,
                                                       const MgCtl* gate) {
@@ -709,8 +765,8 @@ __global__ void __launch_bounds__(MG_BS) k_mg_coarse(void* out, const void* in, 
     cpx<R> acc = C((R)0, (R)0);
     for (int d = 0; d < MG_NSLOT; ++d) {
         const int kn = block_nbr(m, k, d);
-        const long row = (((long)k * MG_NSLOT + d) * n2 + r) * n2;
-        for (int c = 0; c < n2; ++c) cfma(acc, ldc<P>(Mc, row + c), ldc<P>(in, (long)kn * n2 + c));
+        const long base = ((long)k * MG_NSLOT + d) * n2 * n2 + r;
+        for (int c = 0; c < n2; ++c) cfma(acc, ldc<P>(Mc, base + (long)c * n2), ldc<P>(in, (long)kn * n2 + c));
     }
     stc<P>(out, gi, acc);
 }
@@ -849,7 +905,7 @@ __global__ void __launch_bounds__(MG_BS) k_mg_build(const __grid_constant__ Buil
         block_sums<4 * NV>(acc, red, tot);
         if (threadIdx.x < n2) {
             const int hr = threadIdx.x / nv, j = threadIdx.x % nv;
-            const long q = (((long)k * MG_NSLOT + d) * n2 + threadIdx.x) * n2 + cs;
+            const long q = (((long)k * MG_NSLOT + d) * n2 + cs) * n2 + threadIdx.x;   // [k][slot][column][row]
             stc<P>(b.Mc, q, C((typename CE<P>::R)tot[2 * (hr * NV + j)], (typename CE<P>::R)tot[2 * (hr * NV + j) + 1]));
         }
     }
@@ -877,6 +933,7 @@ struct tm_mg {
     void* fz = nullptr;                      // preconditioner fine temporaries
     void* frs = nullptr;
     void* fmr = nullptr;
+    double* op_partial = nullptr;            // block partials of the fused minimal-residual dots
     MgCtl* ctl = nullptr;                    // [0] fine GCR, [1] coarse GCR, [2] minimal residual
     MgCtl* h_ctl = nullptr;
     double* partial = nullptr;
@@ -930,8 +987,16 @@ FullOp full_args(const tm_ctx* c, int P, int sign, void* out, const void* in, co
     return a;
 }
 
-cudaError_t full_op(const tm_ctx* c, int P, int sign, void* out, const void* in, const MgCtl* gate, cudaStream_t st) {
-    const FullOp a = full_args(c, P, sign, out, in, gate);
+// blocks of the full-operator kernel
+long full_op_blocks(const tm_ctx* c) { return (2 * c->vh + 127) / 128; }
+
+// mr non-null: fuse the minimal-residual dots (partial: 3 doubles per block)
+cudaError_t full_op(const tm_ctx* c, int P, int sign, void* out, const void* in, const MgCtl* gate, cudaStream_t st,
+                    MgCtl* mr = nullptr, double* partial = nullptr, unsigned int* counter = nullptr) {
+    FullOp a = full_args(c, P, sign, out, in, gate);
+    a.mr = mr;
+    a.partial = partial;
+    a.counter = counter;
     const unsigned nb = (unsigned)((2 * c->vh + 127) / 128);
     if (P == P64) k_full_op<P64><<<nb, 128, 0, st>>>(a);
     else k_full_op<P32><<<nb, 128, 0, st>>>(a);
@@ -991,7 +1056,7 @@ cudaError_t axpby(int P, long n, void* y, double ca, const void* x, double cw, c
 }
 
 // ----- multigrid pieces -------------------------------------------------------
-int nv_bucket(int nvec) { return nvec <= 4 ? 4 : nvec <= 8 ? 8 : 16; }
+int nv_bucket(int nvec) { return nvec <= 4 ? 4 : nvec <= 8 ? 8 : nvec <= 12 ? 12 : 16; }
 
 template <int P>
 cudaError_t restrict_t(const tm_mg* g, void* coarse, const void* fine, const MgCtl* gate, cudaStream_t st) {
@@ -999,6 +1064,7 @@ cudaError_t restrict_t(const tm_mg* g, void* coarse, const void* fine, const MgC
     const int bs = g->m.Vb >= MG_BS ? MG_BS : ((g->m.Vb + 31) / 32) * 32;
     if (nb == 4) k_mg_restrict<P, 4><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
     else if (nb == 8) k_mg_restrict<P, 8><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
+    else if (nb == 12) k_mg_restrict<P, 12><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
     else k_mg_restrict<P, 16><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
     return cudaGetLastError();
 }
@@ -1028,6 +1094,7 @@ cudaError_t build_t(const tm_mg* g, const BuildArgs& b, cudaStream_t st) {
     const dim3 grid(g->m.Nb, 2 * g->p.nvec);
     if (nb == 4) k_mg_build<P, 4><<<grid, bs, 0, st>>>(b);
     else if (nb == 8) k_mg_build<P, 8><<<grid, bs, 0, st>>>(b);
+    else if (nb == 12) k_mg_build<P, 12><<<grid, bs, 0, st>>>(b);
     else k_mg_build<P, 16><<<grid, bs, 0, st>>>(b);
     return cudaGetLastError();
 }
@@ -1153,10 +1220,8 @@ tm_status mr_steps(tm_mg* g, void* z, const void* r, int steps, cudaStream_t st)
     MCK(full_op(c, P, g->p.sign, g->fmr, z, nullptr, st));
     MCK(axpby(P, n, g->frs, 1.0, r, -1.0, g->fmr, nullptr, st));
     for (int k = 0; k < steps; ++k) {
-        MCK(full_op(c, P, g->p.sign, g->fmr, g->frs, nullptr, st));
-        const void* u[2] = {g->fmr, g->fmr};
-        const void* v[2] = {g->frs, g->fmr};
-        MCK(dots_any(P, n, 2, u, v, MGF_MR, ctl, nullptr, g->partial, g->counter, st));
+        // mr = M r with <mr, r> and <mr, mr> reduced in the same kernel (alpha in ctl)
+        MCK(full_op(c, P, g->p.sign, g->fmr, g->frs, nullptr, st, ctl, g->op_partial, g->counter));
         if (P == P64) k_mr_update<P64><<<flat_grid(n), MG_BS, 0, st>>>(n, z, g->frs, g->fmr, ctl);
         else k_mr_update<P32><<<flat_grid(n), MG_BS, 0, st>>>(n, z, g->frs, g->fmr, ctl);
         MCK(cudaGetLastError());
@@ -1287,6 +1352,7 @@ extern "C" tm_status tm_mg_create(tm_mg** out, tm_ctx* c, const tm_mg_params* p)
     e = e ? e : cudaMalloc(&g->ctl, 3 * sizeof(MgCtl));
     e = e ? e : cudaMallocHost(&g->h_ctl, 3 * sizeof(MgCtl));
     e = e ? e : cudaMalloc(&g->partial, sizeof(double) * MG_GRID_CAP * MG_PART_W);
+    e = e ? e : cudaMalloc(&g->op_partial, sizeof(double) * 3 * full_op_blocks(c));
     e = e ? e : cudaMalloc(&g->counter, sizeof(unsigned int));
     e = e ? e : cudaMemset(g->counter, 0, sizeof(unsigned int));
     e = e ? e : cudaMemset(g->ctl, 0, 3 * sizeof(MgCtl));
@@ -1313,6 +1379,7 @@ extern "C" tm_status tm_mg_destroy(tm_mg* g) {
     cudaFree(g->ctl);
     cudaFreeHost(g->h_ctl);
     cudaFree(g->partial);
+    cudaFree(g->op_partial);
     cudaFree(g->counter);
     delete g;
     return TM_OK;

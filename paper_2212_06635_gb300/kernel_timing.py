@@ -13,6 +13,7 @@ here, and the ncu captures under profiles/ run these same launch sequences.
   ... --multishift                a 12-shift heavy-doublet multishift solve (--prec storage)
   ... --mg ITERS                  multigrid setup and ITERS multigrid-preconditioned GCR iterations
   ... --fma                       measured FP64 and FP32 FMA rates of the CUDA cores
+  ... --batch batched|sequential  the uneven batch of 24 light solves (mixed FP16 CG)
 """
 from __future__ import annotations
 
@@ -292,6 +293,43 @@ def mg_solve(dims, block=(4, 4, 4, 4), nvec=12, setup=100, smooth=8, maxiter=20,
         tm.tm_destroy(ctx)
 
 
+def batch_solve(sequential=False, chunk=16, quiet=False):
+    """The uneven batch of 24 light problems (6 each of 8^3x16, 12^3x24, 16^3x32,
+    24^3x48), mixed FP16 CG to 1e-10: one batched solve (or the 24 solves one
+    after another): the launch sequence of the batched kernels."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import configs as CFG
+    from synth import fields as F
+    ws = CFG.batch_workloads()
+    ctxs, bs, xs = [], [], []
+    try:
+        for w in ws:
+            c = tm.tm_create(w.dims, 0)
+            ctxs.append(c)
+            tm.tm_gauge_load(c, F.gauge_field(w.dims, w.link_seed, workers=1), 1.0)
+            tm.tm_clover_compute(c, w.kappa, w.csw, mu=w.mu, bc_t=w.bc_t)
+            tm.tm_autotune(c, tm.TM_F16, 1)
+            bs.append(torch.from_numpy(F.odd_spinor(w.dims, w.rhs_seed).view(np.float64).copy()).cuda())
+            xs.append(torch.zeros_like(bs[-1]))
+        sp = tm.solve_params(tol=1e-10, sloppy=tm.TM_F16, chunk=chunk)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        if sequential:
+            infos = [tm.tm_solve_cg(c, tm.TM_MDAGM, sp, x, b, check=False) for c, x, b in zip(ctxs, xs, bs)]
+        else:
+            infos = tm.tm_solve_batch(ctxs, tm.TM_MDAGM, sp, xs, bs, check=False)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if not quiet:
+            print(f"uneven batch of {len(ws)}, {'sequential' if sequential else 'batched'}, chunk {chunk}: {dt:.4f} s, "
+                  f"iterations {[i.iters for i in infos]}, reliable updates {[i.reliable_updates for i in infos]}")
+        return dt
+    finally:
+        for c in ctxs:
+            tm.tm_destroy(c)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--dims", type=int, nargs=4, default=[32, 32, 32, 32])
@@ -309,6 +347,9 @@ def main():
     ap.add_argument("--mg", type=int, default=0, metavar="ITERS",
                     help="multigrid setup, then ITERS iterations of multigrid-preconditioned GCR")
     ap.add_argument("--setup", type=int, default=100, help="--mg: minimal-residual steps per near-null vector")
+    ap.add_argument("--batch", choices=["batched", "sequential"], default=None,
+                    help="the uneven batch of 24 light solves, batched or one after another")
+    ap.add_argument("--chunk", type=int, default=16, help="--batch: iterations between host checks")
     ap.add_argument("--fma", action="store_true", help="measured FP64 and FP32 FMA rates")
     a = ap.parse_args()
     dims = tuple(a.dims)
@@ -328,6 +369,8 @@ def main():
         multishift(dims, prec)
     elif a.mg:
         mg_solve(dims, setup=a.setup, maxiter=a.mg)
+    elif a.batch:
+        batch_solve(sequential=a.batch == "sequential", chunk=a.chunk)
     elif a.fma:
         from paper_2212_06635_gb300 import tm
         for p, name in ((0, "FP64"), (1, "FP32")):

@@ -47,3 +47,8 @@ def batch_workloads():
 
 
 N_SHIFTS = 12
+
+
+# two-level multigrid of the full operator at 48^3x96 (the PTC workload's action)
+MG_PARAMS = dict(block=(4, 4, 4, 4), nvec=12, setup_steps=100, smooth_steps=8, coarse_tol=0.1,
+                 coarse_maxiter=30, coarse_restart=16, restart=16, maxiter=1500)
