@@ -13,6 +13,9 @@
 #include <cstring>
 #include <numeric>
 #include <vector>
+#include <mutex>
+#include <map>
+#include <string>
 
 #include "force.h"
 #include "rational.h"
@@ -1550,45 +1553,92 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
     VecBatch<MAXP> pu{}, up{};
     int s1, s2;
     normal_signs(op, &s1, &s2);
-    // one kernel variant per pass for the whole batch: the choice of the context
-    // with the most sites, whose problem dominates the batch's time (a small
-    // lattice's timing-based choice can differ and is noisy)
-    int qbig = 0;
-    for (int q = 1; q < n; ++q)
-        if (cs[q]->vh > cs[qbig]->vh) qbig = q;
-    const int v1 = cs[qbig]->variant[PS][0][K1_EO_INV], v2 = cs[qbig]->variant[PS][0][K2_OE_LOCAL];
+    // Problem tables for a stencil variant per pass (0 direct, 1 staged).  The
+    // variants are tuned on the batch itself: the batched passes of a mixed-size
+    // batch behave unlike any one member's (the small lattices' blocks fill the
+    // large one's tail), so both variants of both passes are timed on the
+    // batch's own tables, with the passes that have no side effects on the solver
+    // state (the even pass and the second odd pass).  The choice is kept per batch
+    // composition and precision.
     int ob1 = 0, ob2 = 0, vbk = 0;
-    for (int q = 0; q < n; ++q) {
-        tm_ctx* c = cs[q];
-        const int nb1 = nblk(c->vh, v1 ? STAGED_BS : DSLASH_BS), nb2 = nblk(c->vh, v2 ? STAGED_BS : DSLASH_BS);
-        const int nbb = nblk(c->vh, BLAS_BS);
-        SolverCtl* ctl = c->ctl;
-        k1.blk_start[q] = k1b.blk_start[q] = ob1;
-        k2a.blk_start[q] = k2b.blk_start[q] = ob2;
-        pu.blk_start[q] = up.blk_start[q] = vbk;
-        k1.p[q] = make_prob(c, PS, 1, K1_EO_INV, s1, w[q].tes, w[q].ps, nullptr, ctl, false);
-        k2a.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s1, w[q].mids, w[q].tes, w[q].ps, ctl, true);
-        k1b.p[q] = make_prob(c, PS, 1, K1_EO_INV, s2, w[q].tes, w[q].mids, nullptr, ctl, false);
-        k2b.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s2, w[q].aps, w[q].tes, w[q].mids, ctl, false);
-        k1.p[q].nblk = k1b.p[q].nblk = nb1;
-        k2a.p[q].nblk = k2b.p[q].nblk = nb2;
-        VecBatch<1> a = vb1(c, w[q].ps, w[q].rs);
-        pu.p[q] = a.p[0];
-        VecBatch<1> u = vb1(c, w[q].xs, w[q].ps, w[q].rs, w[q].aps);
-        up.p[q] = u.p[0];
-        if (done[q]) {   // done problems: a control word that stays stopped
-            c->h_ctl->flag = CTL_STOP;
-            CKS(put_ctl(c, st));
+    auto build_tables = [&](int v1, int v2) -> tm_status {
+        ob1 = ob2 = vbk = 0;
+        for (int q = 0; q < n; ++q) {
+            tm_ctx* c = cs[q];
+            const int nb1 = nblk(c->vh, v1 ? STAGED_BS : DSLASH_BS), nb2 = nblk(c->vh, v2 ? STAGED_BS : DSLASH_BS);
+            const int nbb = nblk(c->vh, BLAS_BS);
+            SolverCtl* ctl = c->ctl;
+            k1.blk_start[q] = k1b.blk_start[q] = ob1;
+            k2a.blk_start[q] = k2b.blk_start[q] = ob2;
+            pu.blk_start[q] = up.blk_start[q] = vbk;
+            k1.p[q] = make_prob(c, PS, 1, K1_EO_INV, s1, w[q].tes, w[q].ps, nullptr, ctl, false);
+            k2a.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s1, w[q].mids, w[q].tes, w[q].ps, ctl, true);
+            k1b.p[q] = make_prob(c, PS, 1, K1_EO_INV, s2, w[q].tes, w[q].mids, nullptr, ctl, false);
+            k2b.p[q] = make_prob(c, PS, 1, K2_OE_LOCAL, s2, w[q].aps, w[q].tes, w[q].mids, ctl, false);
+            k1.p[q].nblk = k1b.p[q].nblk = nb1;
+            k2a.p[q].nblk = k2b.p[q].nblk = nb2;
+            VecBatch<1> a = vb1(c, w[q].ps, w[q].rs);
+            pu.p[q] = a.p[0];
+            VecBatch<1> u = vb1(c, w[q].xs, w[q].ps, w[q].rs, w[q].aps);
+            up.p[q] = u.p[0];
+            ob1 += nb1;
+            ob2 += nb2;
+            vbk += nbb;
         }
-        ob1 += nb1;
-        ob2 += nb2;
-        vbk += nbb;
+        for (auto* t : {&k1, &k1b}) { t->n = n; t->blk_start[n] = ob1; t->fin = FIN_NONE; }
+        for (auto* t : {&k2a, &k2b}) { t->n = n; t->blk_start[n] = ob2; t->fin = FIN_NONE; }
+        k2a.fin = FIN_CG_ALPHA;
+        pu.n = up.n = n;
+        pu.blk_start[n] = up.blk_start[n] = vbk;
+        return TM_OK;
+    };
+    for (int q = 0; q < n; ++q)
+        if (done[q]) {   // done problems: a control word that stays stopped
+            cs[q]->h_ctl->flag = CTL_STOP;
+            CKS(put_ctl(cs[q], st));
+        }
+    int v1 = 0, v2 = 0;
+    if (PS != P64) {
+        std::string key = std::to_string(PS);
+        for (int q = 0; q < n; ++q)
+            key += " " + std::to_string(cs[q]->g.X) + "x" + std::to_string(cs[q]->g.Y) + "x" +
+                   std::to_string(cs[q]->g.Z) + "x" + std::to_string(cs[q]->g.T);
+        static std::mutex tune_mu;
+        static std::map<std::string, std::pair<int, int>> tuned;
+        std::lock_guard<std::mutex> lock(tune_mu);
+        auto it = tuned.find(key);
+        if (it != tuned.end()) {
+            v1 = it->second.first;
+            v2 = it->second.second;
+        } else {
+            cudaEvent_t e0, e1, e2;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            CK(cudaEventCreate(&e2));
+            float best1 = 1e30f, best2 = 1e30f;
+            for (int v = 0; v < 2; ++v) {
+                CKS(build_tables(v, v));
+                CK((launch_pass<PS, 1, K1_EO_INV, MAXP>(v, k1, ob1, st)));     // warm-up
+                CK((launch_pass<PS, 1, K2_OE_LOCAL, MAXP>(v, k2b, ob2, st)));
+                CK(cudaEventRecord(e0, st));
+                for (int r = 0; r < 3; ++r) CK((launch_pass<PS, 1, K1_EO_INV, MAXP>(v, k1, ob1, st)));
+                CK(cudaEventRecord(e1, st));
+                for (int r = 0; r < 3; ++r) CK((launch_pass<PS, 1, K2_OE_LOCAL, MAXP>(v, k2b, ob2, st)));
+                CK(cudaEventRecord(e2, st));
+                CK(cudaEventSynchronize(e2));
+                float t1 = 0.f, t2 = 0.f;
+                CK(cudaEventElapsedTime(&t1, e0, e1));
+                CK(cudaEventElapsedTime(&t2, e1, e2));
+                if (t1 < best1) { best1 = t1; v1 = v; }
+                if (t2 < best2) { best2 = t2; v2 = v; }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cudaEventDestroy(e2);
+            tuned[key] = {v1, v2};
+        }
     }
-    for (auto* t : {&k1, &k1b}) { t->n = n; t->blk_start[n] = ob1; t->fin = FIN_NONE; }
-    for (auto* t : {&k2a, &k2b}) { t->n = n; t->blk_start[n] = ob2; t->fin = FIN_NONE; }
-    k2a.fin = FIN_CG_ALPHA;
-    pu.n = up.n = n;
-    pu.blk_start[n] = up.blk_start[n] = vbk;
+    CKS(build_tables(v1, v2));
     auto iteration = [&]() -> cudaError_t {
         cudaError_t e = launch_cg_pupdate<PS, NC, MAXP>(pu, vbk, st);
         if (!e) e = launch_pass<PS, 1, K1_EO_INV, MAXP>(v1, k1, ob1, st);
