@@ -55,3 +55,32 @@ def test_reference_arm_prints_one_json_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["value"] > 0 and d["unit"] == "GB/s"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_parity_lex_matches_the_half_lattice_order():
+    """The bench embeds odd-site fields into full canonical fields with
+    _parity_lex: site k of a parity must be the k-th site of that parity in
+    lexicographic order (the native half-lattice order, lex // 2 == k)."""
+    import numpy as np
+    import torch
+    sys.path.insert(0, ROOT)
+    import bench
+    from oracle import dirac as D
+    for dims in ((4, 4, 4, 4), (6, 4, 2, 8), (2, 6, 4, 2)):
+        geo = D.Geometry(dims)
+        for parity, ref in ((0, geo.even), (1, geo.odd)):
+            got = bench._parity_lex(dims, parity, torch.device("cpu")).numpy()
+            assert np.array_equal(got, ref), (dims, parity)
+
+
+def test_workload_summary_keeps_the_times():
+    sys.path.insert(0, ROOT)
+    import bench
+    extra = {"batch_uneven_24": {"batched_s": 0.48, "sequential_s": 0.59},
+             "mg_gcr_48x96": {"mg_setup_s": 5.9, "mg_gcr_s": 28.9, "mg_gcr_iters": 381, "eo_mixed_cg_s": 1.08,
+                              "speedup_mg_vs_eo_mixed_cg": 0.037, "mg_gcr": {"iters": 381}},
+             "ptc_fcg_48x96": {"error": "RuntimeError('x')"}}
+    out = bench.summarize(extra)
+    assert out["batch_24_s"] == {"batched": 0.48, "sequential": 0.59}
+    assert out["mg_48x96"]["mg_gcr_iters"] == 381 and "mg_gcr" not in out["mg_48x96"]
+    assert out["ptc_48x96"]["error"].startswith("RuntimeError")
