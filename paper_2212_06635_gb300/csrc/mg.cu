@@ -81,10 +81,11 @@ struct MgCtl {
     double rr;                 // residual norm^2
     double stop_rr;            // stop when rr < stop_rr
     double nrm2;
+    double tol2;               // relative tolerance squared (MGF_RRB sets stop_rr from it)
     int iter, maxiter, flag, pad;
 };
 
-enum MgFin { MGF_DOTS = 0, MGF_MR = 1, MGF_GCR = 2, MGF_RR = 3, MGF_NRM = 4, MGF_RR0 = 5 };
+enum MgFin { MGF_DOTS = 0, MGF_MR = 1, MGF_GCR = 2, MGF_RR = 3, MGF_NRM = 4, MGF_RR0 = 5, MGF_RRB = 6 };
 
 __device__ inline void mg_finalize(int fin, const double* t, int np, MgCtl* c) {
     switch (fin) {
@@ -131,6 +132,11 @@ __device__ inline void mg_finalize(int fin, const double* t, int np, MgCtl* c) {
             break;
         case MGF_NRM:
             c->nrm2 = t[0];
+            break;
+        case MGF_RRB:    // start of a solve from x = 0: r = b, stop relative to ||b||
+            c->rr = t[0];
+            c->stop_rr = c->tol2 * t[0];
+            if (!(t[0] > 0.0) || !isfinite(t[0])) c->flag = CTL_STOP;   // b = 0 (x = 0 is the solution) or not finite
             break;
         default:
             break;
@@ -247,6 +253,15 @@ __global__ void __launch_bounds__(MG_BS) k_pairdots(const __grid_constant__ Pair
         *a.counter = 0u;
         mg_finalize(a.fin, tot, a.np, a.ctl);
     }
+}
+
+// a level's control word at the start of a device-driven solve
+__global__ void k_ctl_start(MgCtl* c, int maxiter, double tol2) {
+    c->iter = 0;
+    c->maxiter = maxiter;
+    c->tol2 = tol2;
+    c->flag = CTL_RUN;
+    c->na = 1.0;
 }
 
 // y = ca x + cw w (real host scalars; x or w may be null)
@@ -684,47 +699,51 @@ __global__ void __launch_bounds__(MG_BS) k_mg_orth(void* Pm, MgGeom m) {
     }
 }
 
-// coarse = P^+ fine: one CUDA block per lattice block k, rows r = h nvec + j,
-// one chirality at a time (a thread holds the nvec sums of one chirality)
-template <int P, int NV>
-__global__ void __launch_bounds__(MG_BS, 2) k_mg_restrict(void* coarse, const void* fine, const void* Pm, MgGeom m,
-                                                           const MgCtl* gate) {
+// coarse = P^+ fine: one CUDA block per lattice block k with one warp per row
+// r = h nvec + j (2 nvec warps).  The block's fine sites are staged in shared
+// memory (component-major, a chunk of sites at a time); each warp's lanes stride
+// over the entries of its prolongator column, which are contiguous in the
+// [a][j][c][s] layout, and the row sum is a warp shuffle reduction in FP64.
+template <int P>
+__global__ void __launch_bounds__(1024) k_mg_restrict(void* coarse, const void* fine, const void* Pm, MgGeom m,
+                                                       const MgCtl* gate) {
     using R = typename PT<P>::R;
+    constexpr int CH = P == P64 ? 128 : 256;   // sites per staged chunk (24 KB either way)
     if (gate && gate->flag != CTL_RUN) return;
+    __shared__ cpx<R> sf[12 * CH];
     const int k = blockIdx.x;
     const int nv = m.nvec;
-    __shared__ double red[(MG_BS / 32) * 2 * NV];
-    __shared__ double tot[2 * NV];
-    for (int h = 0; h < 2; ++h) {
-        R accr[2 * NV];   // per-thread sums (a thread covers Vb / blockDim sites) in the arithmetic precision
-#pragma unroll
-        for (int q = 0; q < 2 * NV; ++q) accr[q] = (R)0;
-        for (int s = threadIdx.x; s < m.Vb; s += blockDim.x) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int h = warp / nv, j = warp % nv;
+    const long col = p_index(m, 2 * k + h, j, 0, 0);
+    cpx<R> acc = C((R)0, (R)0);
+    for (int s0 = 0; s0 < m.Vb; s0 += CH) {
+        const int ns = min(CH, m.Vb - s0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < ns; t += blockDim.x) {
             int x[4];
-            block_site(m, k, s, x);
+            block_site(m, k, s0 + t, x);
             const int par = (x[0] + x[1] + x[2] + x[3]) & 1;
-            cpx<R> v[6];   // spins 2h, 2h+1 (reals 12 h .. 12 h + 11)
-            load_reals<P, 12>(reinterpret_cast<const char*>(fine) + (size_t)par * m.half, m.g.vh, lex_of(m.g, x) >> 1,
-                              12 * h, reinterpret_cast<R*>(v));
+            cpx<R> v[12];
+            load_spinor<P, 12>(reinterpret_cast<const char*>(fine) + (size_t)par * m.half, m.g.vh,
+                               lex_of(m.g, x) >> 1, v);
 #pragma unroll
-            for (int j = 0; j < NV; ++j) {
-                if (j < nv) {
-                    cpx<R> t = C((R)0, (R)0);
-#pragma unroll
-                    for (int c = 0; c < 6; ++c) cfma_cj(t, ldc<P>(Pm, p_index(m, 2 * k + h, j, c, s)), v[c]);
-                    accr[2 * j] += t.re;
-                    accr[2 * j + 1] += t.im;
-                }
-            }
+            for (int q = 0; q < 12; ++q) sf[q * CH + t] = v[q];
         }
-        double acc[2 * NV];
-#pragma unroll
-        for (int q = 0; q < 2 * NV; ++q) acc[q] = (double)accr[q];
-        block_sums<2 * NV>(acc, red, tot);
-        if (threadIdx.x < nv)
-            stc<P>(coarse, (long)k * 2 * nv + h * nv + threadIdx.x,
-                   C((typename CE<P>::R)tot[2 * threadIdx.x], (typename CE<P>::R)tot[2 * threadIdx.x + 1]));
+        __syncthreads();
+        for (int e = lane; e < 6 * ns; e += 32) {
+            const int c = e / ns, sl = e - c * ns;
+            cfma_cj(acc, ldc<P>(Pm, col + (long)c * m.Vb + s0 + sl), sf[(6 * h + c) * CH + sl]);
+        }
     }
+    double re = (double)acc.re, im = (double)acc.im;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        re += __shfl_xor_sync(0xffffffffu, re, o);
+        im += __shfl_xor_sync(0xffffffffu, im, o);
+    }
+    if (lane == 0)
+        stc<P>(coarse, (long)k * 2 * nv + warp, C((typename CE<P>::R)re, (typename CE<P>::R)im));
 }
 
 // fine = P coarse: one thread per (block, site)
@@ -938,7 +957,8 @@ struct tm_mg {
     MgCtl* h_ctl = nullptr;
     double* partial = nullptr;
     unsigned int* counter = nullptr;
-    long coarse_iters = 0;                   // coarse GCR iterations since the last reset
+    cudaStream_t cap = nullptr;              // private stream for graph capture
+    cudaGraphExec_t coarse_graph = nullptr;  // the whole coarse solve (restrict output -> x)
 };
 
 namespace {
@@ -1060,12 +1080,7 @@ int nv_bucket(int nvec) { return nvec <= 4 ? 4 : nvec <= 8 ? 8 : nvec <= 12 ? 12
 
 template <int P>
 cudaError_t restrict_t(const tm_mg* g, void* coarse, const void* fine, const MgCtl* gate, cudaStream_t st) {
-    const int nb = nv_bucket(g->p.nvec);
-    const int bs = g->m.Vb >= MG_BS ? MG_BS : ((g->m.Vb + 31) / 32) * 32;
-    if (nb == 4) k_mg_restrict<P, 4><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
-    else if (nb == 8) k_mg_restrict<P, 8><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
-    else if (nb == 12) k_mg_restrict<P, 12><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
-    else k_mg_restrict<P, 16><<<g->m.Nb, bs, 0, st>>>(coarse, fine, g->Pm, g->m, gate);
+    k_mg_restrict<P><<<g->m.Nb, 64 * g->p.nvec, 0, st>>>(coarse, fine, g->Pm, g->m, gate);   // 2 nvec warps
     return cudaGetLastError();
 }
 
@@ -1203,14 +1218,6 @@ tm_status gcr_run(tm_mg* g, Level& L, int level, GcrWork& w, int restart, double
     }
 }
 
-struct CoarseLevel : Level {
-    tm_mg* g;
-    tm_status apply(void* y, const void* x, cudaStream_t st) override {
-        MCK(mg_coarse(g, y, x, ctl, st));
-        return TM_OK;
-    }
-};
-
 // minimal-residual steps on M z = r from the given z (the oracle's minimal_residual)
 tm_status mr_steps(tm_mg* g, void* z, const void* r, int steps, cudaStream_t st) {
     tm_ctx* c = g->c;
@@ -1230,34 +1237,102 @@ tm_status mr_steps(tm_mg* g, void* z, const void* r, int steps, cudaStream_t st)
 }
 
 // z = P M_c^-1 P^+ r (coarse GCR to coarse_tol), then smooth_steps MR steps
-tm_status mg_apply(tm_mg* g, void* z, const void* r, cudaStream_t st) {
+// The coarse solve is launch-bound (kernels of a few microseconds on vectors of
+// ~1e6 complex entries), so the whole of it is one CUDA graph: control word
+// reset, x = 0, r = b, ||b||^2 (stop threshold set on the device), then
+// ceil(coarse_maxiter / restart) restart cycles of GCR iterations and true
+// residuals.  Every kernel is gated on the coarse control word, so the
+// iterations after convergence or the iteration bound exit at entry.  Captured
+// once per hierarchy on its private stream; its vectors are the hierarchy's own.
+tm_status coarse_graph(tm_mg* g) {
+    if (g->coarse_graph) return TM_OK;
+    const int P = g->P;
+    const long n = g->ncoarse;
+    const int R = g->p.coarse_restart;
+    const int ncyc = (g->p.coarse_maxiter + R - 1) / R;
+    MgCtl* ctl = g->ctl + 1;
     GcrWork w{};
     w.x = g->cvec[0];
     w.r = g->cvec[1];
     w.b = g->cvec[2];
     w.t = g->cvec[3];
-    const int R = g->p.coarse_restart;
     for (int i = 0; i < R; ++i) {
         w.p[i] = g->cvec[4 + i];
         w.ap[i] = g->cvec[4 + R + i];
     }
-    MCK(mg_restrict(g, w.b, r, nullptr, st));
-    const void* u[1] = {w.b};
-    MCK(dots_any(g->P, g->ncoarse, 1, u, u, MGF_NRM, g->ctl + 1, nullptr, g->partial, g->counter, st));
-    MCKS(read_ctl(g, 1, st));
-    const double bb = g->h_ctl[1].nrm2;
-    if (bb > 0.0 && std::isfinite(bb)) {
-        CoarseLevel L;
-        L.g = g;
-        L.n = g->ncoarse;
-        L.P = g->P;
-        L.ctl = g->ctl + 1;
-        MCKS(gcr_run(g, L, 1, w, R, g->p.coarse_tol * g->p.coarse_tol * bb, g->p.coarse_maxiter, false, st));
-        g->coarse_iters += g->h_ctl[1].iter;
-    } else {
-        MCK(axpby(g->P, g->ncoarse, w.x, 0.0, nullptr, 0.0, nullptr, nullptr, st));
+    const cudaStream_t st = g->cap;
+    cudaGraph_t graph = nullptr;
+    MCK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    auto body = [&]() -> cudaError_t {
+        k_ctl_start<<<1, 1, 0, st>>>(ctl, g->p.coarse_maxiter, g->p.coarse_tol * g->p.coarse_tol);
+        cudaError_t e = cudaGetLastError();
+        if (!e) e = axpby(P, n, w.x, 0.0, nullptr, 0.0, nullptr, nullptr, st);
+        if (!e) e = axpby(P, n, w.r, 1.0, w.b, 0.0, nullptr, nullptr, st);
+        const void* ub[1] = {w.r};
+        if (!e) e = dots_any(P, n, 1, ub, ub, MGF_RRB, ctl, nullptr, g->partial, g->counter, st);
+        for (int cyc = 0; cyc < ncyc && !e; ++cyc) {
+            for (int i = 0; i < R && !e; ++i) {
+                e = axpby(P, n, w.p[i], 1.0, w.r, 0.0, nullptr, ctl, st);   // no coarse preconditioner
+                if (!e) e = mg_coarse(g, w.ap[i], w.p[i], ctl, st);
+                if (i > 0 && !e) {
+                    const void* u[MG_MAX_RESTART];
+                    const void* v[MG_MAX_RESTART];
+                    PtrList pl{}, al{};
+                    for (int j = 0; j < i; ++j) {
+                        u[j] = w.ap[j];
+                        v[j] = w.ap[i];
+                        pl.q[j] = w.p[j];
+                        al.q[j] = w.ap[j];
+                    }
+                    e = dots_any(P, n, i, u, v, MGF_DOTS, ctl, ctl, g->partial, g->counter, st);
+                    if (!e) {
+                        if (P == P64) k_gcr_orth<P64><<<flat_grid(n), MG_BS, 0, st>>>(n, i, w.p[i], w.ap[i], pl, al, ctl);
+                        else k_gcr_orth<P32><<<flat_grid(n), MG_BS, 0, st>>>(n, i, w.p[i], w.ap[i], pl, al, ctl);
+                        e = cudaGetLastError();
+                    }
+                }
+                const void* u2[2] = {w.ap[i], w.ap[i]};
+                const void* v2[2] = {w.ap[i], w.r};
+                if (!e) e = dots_any(P, n, 2, u2, v2, MGF_GCR, ctl, ctl, g->partial, g->counter, st);
+                if (!e) {
+                    if (P == P64)
+                        k_gcr_update<P64><<<flat_grid(n), MG_BS, 0, st>>>(n, w.p[i], w.ap[i], w.x, w.r, ctl, g->partial, g->counter);
+                    else
+                        k_gcr_update<P32><<<flat_grid(n), MG_BS, 0, st>>>(n, w.p[i], w.ap[i], w.x, w.r, ctl, g->partial, g->counter);
+                    e = cudaGetLastError();
+                }
+            }
+            if (cyc + 1 < ncyc && !e) {   // restart from the true residual
+                e = mg_coarse(g, w.t, w.x, ctl, st);
+                if (!e) e = axpby(P, n, w.r, 1.0, w.b, -1.0, w.t, ctl, st);
+                const void* u[1] = {w.r};
+                if (!e) e = dots_any(P, n, 1, u, u, MGF_RR0, ctl, ctl, g->partial, g->counter, st);
+            }
+        }
+        return e;
+    };
+    const cudaError_t e = body();
+    const cudaError_t e2 = cudaStreamEndCapture(st, &graph);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (graph) cudaGraphDestroy(graph);
+        return tmk_failf(TM_ERR_CUDA, "multigrid: capture of the coarse solve: %s",
+                         cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    MCK(mg_prolong(g, z, w.x, nullptr, st));
+    const cudaError_t e3 = cudaGraphInstantiate(&g->coarse_graph, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e3 != cudaSuccess) {
+        g->coarse_graph = nullptr;
+        return tmk_failf(TM_ERR_CUDA, "multigrid: coarse graph: %s", cudaGetErrorString(e3));
+    }
+    return TM_OK;
+}
+
+// z = P M_c^-1 P^+ r (coarse GCR to coarse_tol), then smooth_steps MR steps
+tm_status mg_apply(tm_mg* g, void* z, const void* r, cudaStream_t st) {
+    MCKS(coarse_graph(g));
+    MCK(mg_restrict(g, g->cvec[2], r, nullptr, st));
+    MCK(cudaGraphLaunch(g->coarse_graph, st));
+    MCK(mg_prolong(g, z, g->cvec[0], nullptr, st));
     if (g->p.smooth_steps > 0) MCKS(mr_steps(g, z, r, g->p.smooth_steps, st));
     return TM_OK;
 }
@@ -1356,6 +1431,7 @@ extern "C" tm_status tm_mg_create(tm_mg** out, tm_ctx* c, const tm_mg_params* p)
     e = e ? e : cudaMalloc(&g->counter, sizeof(unsigned int));
     e = e ? e : cudaMemset(g->counter, 0, sizeof(unsigned int));
     e = e ? e : cudaMemset(g->ctl, 0, 3 * sizeof(MgCtl));
+    e = e ? e : cudaStreamCreateWithFlags(&g->cap, cudaStreamNonBlocking);
     if (e != cudaSuccess) {
         tm_mg_destroy(g);
         return tmk_failf(e == cudaErrorMemoryAllocation ? TM_ERR_OOM : TM_ERR_CUDA, "tm_mg_create: %s",
@@ -1378,6 +1454,8 @@ extern "C" tm_status tm_mg_destroy(tm_mg* g) {
     cudaFree(g->fmr);
     cudaFree(g->ctl);
     cudaFreeHost(g->h_ctl);
+    if (g->coarse_graph) cudaGraphExecDestroy(g->coarse_graph);
+    if (g->cap) cudaStreamDestroy(g->cap);
     cudaFree(g->partial);
     cudaFree(g->op_partial);
     cudaFree(g->counter);
@@ -1518,11 +1596,10 @@ extern "C" tm_status tm_mg_precondition(tm_mg* g, double* z, const double* r, in
     void* rn;
     MCKS(tmk_ws_get(g->c, WS_MG_IN, g->fbytes, &rn));
     MCK(full_import(g->c, g->P, rn, r, st));
-    g->coarse_iters = 0;
     MCKS(mg_apply(g, g->fz, rn, st));
     MCK(full_export(g->c, g->P, z, g->fz, st));
-    MCK(cudaStreamSynchronize(st));
-    if (coarse_iters) *coarse_iters = (int)g->coarse_iters;
+    MCKS(read_ctl(g, 1, st));
+    if (coarse_iters) *coarse_iters = g->h_ctl[1].iter;
     return TM_OK;
 }
 

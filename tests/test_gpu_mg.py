@@ -273,6 +273,32 @@ def test_fp32_multigrid_and_gcr_solves():
         p.close()
 
 
+def test_fp32_preconditioner_and_minus_sign_solve():
+    """FP32 hierarchy of M(-mu): the preconditioner against the oracle's built
+    from the GPU's own (FP32-smoothed) vectors with an essentially exact coarse
+    solve (FP32 tolerance), and the preconditioned GCR solve of M(-mu) x = b to
+    an oracle residual of 1e-10."""
+    import torch
+    dims = (4, 4, 4, 8)
+    p = _Pair(dims, (2, 2, 2, 2), 6, setup_steps=10, smooth_steps=3, sign=-1, prec=1, coarse_tol=1e-7,
+              oracle_from_gpu_vectors=True, seed=1981)
+    try:
+        tm = p.tm
+        r = _full(dims, 82)
+        z = torch.empty(p.V * 24, dtype=torch.float64, device="cuda")
+        tm.tm_mg_precondition(p.mg, z, to_dev(r))
+        assert rel(from_dev(z, r.shape), p.ref.precondition(r)) < 2e-5
+        b = _full(dims, 83)
+        x = torch.zeros(p.V * 24, dtype=torch.float64, device="cuda")
+        info = tm.tm_solve_gcr(p.ctx, -1, p.mg, tm.solve_params(tol=1e-10, maxiter=2000, sloppy=tm.TM_F32, chunk=8),
+                               x, to_dev(b))
+        res = np.linalg.norm(b - p.op.M(from_dev(x, b.shape), -1)) / np.linalg.norm(b)
+        assert res <= 1.05e-10, res
+        assert info.reliable_updates >= 1
+    finally:
+        p.close()
+
+
 def test_multigrid_errors():
     import torch
     from paper_2212_06635_gb300 import tm
