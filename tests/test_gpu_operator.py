@@ -117,6 +117,61 @@ def test_full_size_sampled_32x64(full32, prec):
     assert rel(got, refs["mdagm"]) < tol(prec, 2), (prec, rel(got, refs["mdagm"]))
 
 
+@pytest.fixture(scope="module")
+def heavy24():
+    """24^3x48, the heavy-doublet multishift workload (mubar 0.1246, epsbar 0.1350),
+    and 40 sampled odd sites."""
+    dims = (24, 24, 24, 48)
+    u = F.gauge_field(dims, 1002)
+    op = D.TwistedMassClover(u, dims, 0.1400, CSW, mubar=0.1246, epsbar=0.1350)
+    lat = Lat(u, dims, 0.1400, CSW, mubar=0.1246, epsbar=0.1350)
+    psi = F.odd_spinor(dims, 2002, 2)
+    rng = np.random.default_rng(6)
+    s = np.unique(np.concatenate([[0, lat.vh - 1], rng.integers(0, lat.vh, 38)]))
+    n2 = _two_hop_odd(op.geo, s)
+    mid = np.zeros_like(psi)
+    mid[n2] = op.Qhat_at(psi, n2, -1, heavy=True)
+    refs = {"qh": op.Qhat_at(psi, s, +1, heavy=True), "qhsq": op.Qhat_at(mid, s, +1, heavy=True)}
+    yield lat, psi, s, refs
+    lat.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 3, 2], ids=["f64", "f32", "f16", "bf16"])
+def test_full_size_sampled_heavy_24x48(heavy24, prec):
+    """The heavy doublet at the multishift workload's size, in the variant the
+    autotuner picks (the even pass splits the flavours over thread pairs):
+    Q_hat_h and Q_hat_h Q_hat_h^dag at sampled odd sites."""
+    lat, psi, s, refs = heavy24
+    tm = lat.tm
+    if prec != 0:
+        tm.tm_autotune(lat.ctx, prec, 2)
+    got = lat.apply(tm.TM_QH, prec, psi)[s]
+    assert rel(got, refs["qh"]) < tol(prec), (prec, rel(got, refs["qh"]))
+    got = lat.apply(tm.TM_QH_SQ, prec, psi)[s]
+    assert rel(got, refs["qhsq"]) < tol(prec, 2), (prec, rel(got, refs["qhsq"]))
+
+
+def test_full_size_sampled_48x96_f16():
+    """48^3x96, the learned-preconditioner and multigrid workload (kappa
+    0.1394265, mu 0.00072), in FP16 storage and FP64: Q_hat_+ at sampled odd
+    sites, including the last."""
+    dims = (48, 48, 48, 96)
+    u = F.gauge_field(dims, 1004)
+    op = D.TwistedMassClover(u, dims, 0.1394265, CSW, mu=0.00072)
+    lat = Lat(u, dims, 0.1394265, CSW, mu=0.00072)
+    try:
+        psi = F.odd_spinor(dims, 2004)
+        rng = np.random.default_rng(7)
+        s = np.unique(np.concatenate([[0, lat.vh - 1], rng.integers(0, lat.vh, 30)]))
+        ref = op.Qhat_at(psi, s, +1)
+        lat.tm.tm_autotune(lat.ctx, lat.tm.TM_F16, 1)
+        for prec in (0, 3):
+            got = lat.apply(lat.tm.TM_QHAT_PLUS, prec, psi)[s]
+            assert rel(got, ref) < tol(prec), (prec, rel(got, ref))
+    finally:
+        lat.close()
+
+
 @pytest.mark.parametrize("prec", [1, 3, 2], ids=["f32", "f16", "bf16"])
 def test_staged_variant_matches_oracle(setup, prec):
     """The shared-memory staged stencil kernels give the oracle's operator too
