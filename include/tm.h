@@ -112,7 +112,8 @@ typedef struct {
 } tm_solve_info;
 
 /* Context: one lattice on one device.  dims as above; device = CUDA ordinal.
- * Fails with TM_ERR_ARG for odd or < 2 extents. */
+ * Fails with TM_ERR_ARG for odd or < 2 extents, or a volume of 2^31 sites or
+ * more (site indices are 32-bit). */
 tm_status tm_create(tm_ctx** ctx, const int dims[4], int device);
 tm_status tm_destroy(tm_ctx* ctx);
 

@@ -142,14 +142,15 @@ extern "C" tm_status tm_create(tm_ctx** out, const int dims[4], int device) {
     if (!out || !dims) return fail(TM_ERR_ARG, "tm_create: null argument");
     for (int k = 0; k < 4; ++k)
         if (dims[k] < 2 || dims[k] % 2) return fail(TM_ERR_ARG, "tm_create: extent %d = %d must be even and >= 2", k, dims[k]);
+    if ((double)dims[0] * dims[1] * dims[2] * dims[3] >= 2147483648.0)
+        return fail(TM_ERR_ARG, "tm_create: the volume must be below 2^31 sites");
     CK(cudaSetDevice(device));
     static std::atomic<unsigned long long> next_uid{1};
     tm_ctx* c = new tm_ctx();
     c->uid = next_uid.fetch_add(1);
     c->device = device;
-    c->g.X = dims[0]; c->g.Y = dims[1]; c->g.Z = dims[2]; c->g.T = dims[3];
-    c->vh = (long)dims[0] * dims[1] * dims[2] * dims[3] / 2;
-    c->g.vh = c->vh;
+    geom_init(c->g, dims[0], dims[1], dims[2], dims[3]);
+    c->vh = c->g.vh;
     c->max_blocks = nblk(c->vh, MIN_BS);
     cudaError_t e = cudaSuccess;
     e = e ? e : cudaStreamCreateWithFlags(&c->sstream, cudaStreamNonBlocking);

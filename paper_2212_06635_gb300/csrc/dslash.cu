@@ -50,18 +50,30 @@ __device__ __forceinline__ void hop_mu(cpx<typename PT<P>::R> (&acc)[NF][4][3], 
     for (int f = 0; f < NF; ++f) hop_dir<R, MU, +1, true, SC>(acc[f], psi + 12 * f, u, SC ? ph_b * (R)sc : ph_b);
 }
 
-// Resident blocks the compiler must fit per SM.  Both light 16-bit passes fit in
-// 96 registers (spilling at most 16 B; the even pass streams its inverse blocks
-// two rows at a time for this), which raises occupancy from 4 to 5 blocks of
-// 128 threads.  The two-flavour odd pass fits 4 blocks in 16-bit storage (128
-// registers) and 3 in FP32 (168 registers, 8 B spilled: 94.8 -> 78.1 us at
-// 24^3x48).  The other FP32 and the FP64 passes keep the default.  Sweeps at
-// 32^3x64 (light) and 24^3x48 (heavy) put the optimum at these values.  (The
-// two-flavour even pass splits the flavours over a thread pair: dslash_heavy.cu.)
+// Resident blocks the compiler must fit per SM (128-thread blocks; the register
+// cap follows).  Sweeps at 32^3x64 (light) and 24^3x48 (heavy) put the optimum at:
+//   light 16-bit even pass: 5 blocks (96 registers; the inverse blocks stream two
+//     rows at a time for this).  6 blocks: 112.8 -> 133.4 us FP16, 116.6 -> 174.2 us BF16;
+//   light odd pass: 7 blocks FP16 (72 registers, 16 B spilled) and 6 BF16 (80
+//     registers): 5 / 6 / 7 blocks take 112.2 / 104.9 / 103.0 us FP16 and
+//     126.9 / 113.2 / 119.0 us BF16 (4 blocks: 108.3 / 113.1 us);
+//   light FP32 odd pass: 4 blocks (128 registers, 16 B spilled): 156.5 -> 150.0 us
+//     (3 blocks 152.0 us); the FP32 even pass keeps the default (3 blocks at 156
+//     registers; 4 blocks: 187 -> 227 us);
+//   two-flavour odd pass: 4 blocks in 16-bit storage (128 registers; 3 / 5
+//     blocks: 63.8 -> 67.7 / 75.0 us FP16) and 3 in FP32 (168 registers, 8 B
+//     spilled: 94.8 -> 78.1 us at 24^3x48; 2 / 4 blocks: 94.5 / 84.4 us).
+// The FP64 passes keep the default.  (The two-flavour even pass splits the
+// flavours over a thread pair: dslash_heavy.cu.)
 template <int P, int NF, int KIND>
 constexpr int dslash_min_blocks() {
-    if (P == PF16 || P == PB16) return NF == 1 ? 5 : 4;
-    return (P == P32 && NF == 2 && KIND == K2_OE_LOCAL) ? 3 : 1;
+    if (P == PF16 || P == PB16) {
+        if (NF == 2) return 4;
+        if (KIND == K1_EO_INV) return 5;
+        return P == PF16 ? 7 : 6;
+    }
+    if (P == P32 && KIND == K2_OE_LOCAL) return NF == 2 ? 3 : 4;
+    return 1;
 }
 
 template <int P, int NF, int KIND, int NP, int BS>

@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include "../../include/tm.h"
+#include "fastdiv.h"
 
 namespace tmk {
 
@@ -310,8 +311,17 @@ constexpr int MAXP = 32;
 
 struct Geom {
     int X, Y, Z, T;
-    long vh;
+    long vh;                 // sites per parity; the volume 2 vh is below 2^31
+    FastDiv dxh, dy, dz;     // division by X/2, Y, Z (geom_init)
 };
+
+inline void geom_init(Geom& g, int X, int Y, int Z, int T) {
+    g.X = X; g.Y = Y; g.Z = Z; g.T = T;
+    g.vh = (long)X * Y * Z * T / 2;
+    g.dxh = make_fastdiv((uint32_t)(X / 2));
+    g.dy = make_fastdiv((uint32_t)Y);
+    g.dz = make_fastdiv((uint32_t)Z);
+}
 
 struct OpProb {
     Geom g;
@@ -355,19 +365,21 @@ __device__ __forceinline__ int find_problem(const OpBatch<NP>& b, int blk) {
 struct Coord {
     int x, y, z, t;
 };
+// (32-bit arithmetic throughout: the volume is below 2^31)
 __device__ __forceinline__ Coord cb_coords(const Geom& g, long i, int par) {
-    const int xh2 = g.X >> 1;
-    long r = i / xh2;
-    const int xh = (int)(i - r * xh2);
+    const uint32_t u = (uint32_t)i;
+    const uint32_t r = fdiv(u, g.dxh);       // i / (X/2)
+    const uint32_t q = fdiv(r, g.dy);
+    const uint32_t t = fdiv(q, g.dz);
     Coord c;
-    c.y = (int)(r % g.Y); r /= g.Y;
-    c.z = (int)(r % g.Z);
-    c.t = (int)(r / g.Z);
-    c.x = 2 * xh + ((c.y + c.z + c.t + par) & 1);
+    c.y = (int)(r - q * g.dy.d);
+    c.z = (int)(q - t * g.dz.d);
+    c.t = (int)t;
+    c.x = 2 * (int)(u - r * g.dxh.d) + ((c.y + c.z + c.t + par) & 1);
     return c;
 }
 __device__ __forceinline__ long cb_index(const Geom& g, int x, int y, int z, int t) {
-    return ((((long)t * g.Z + z) * g.Y + y) * g.X + x) >> 1;
+    return (long)((((t * g.Z + z) * g.Y + y) * g.X + x) >> 1);
 }
 
 }  // namespace tmk
