@@ -140,7 +140,7 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(self.rows)}
 
 
-KERNEL_SOURCES = ["tm_internal.h", "tm_kernels.h", "dslash_common.cuh", "dslash.cu", "dslash_staged.cu"]
+KERNEL_SOURCES = ["tm_internal.h", "fastdiv.h", "tm_kernels.h", "dslash_common.cuh", "dslash.cu", "dslash_staged.cu"]
 
 
 def kernel_sources_sha256():
