@@ -421,7 +421,7 @@ def run_ours(args, rank, world, local_rank):
         # ---- seconds to true rel res 1e-10: chosen form vs FP64 CG ----------------
         tts = {}
         if not args.no_solve:
-            forms = [("chosen", prec, "mixed-precision CG: %s storage, FP32 math, FP64 reliable updates"
+            forms = [("chosen", prec, "mixed-precision CG: %s storage, FP32 math, double-word reliable updates, FP64 final residual"
                       % args.storage)]
             if not args.no_fp64:
                 forms.append(("fp64_cg", tm.TM_F64, "plain FP64 CG"))

@@ -185,6 +185,17 @@ tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, 
 tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,
                         void* stream);
 
+/* out = op(in) on native FP64 fields (the layout of tm_apply_Mhat with TM_F64),
+ * evaluated in double-word arithmetic: each real is carried as an unevaluated sum
+ * of two FP32 numbers (a 48-bit significand), in and out are rounded to that on
+ * the way in and out, and links and clover blocks come from double-word copies
+ * made from the FP64 ones when stale.  This is how the mixed-precision solvers
+ * recompute their true residuals between reliable updates (Sec. 4.1's reliable
+ * updates): on this GPU the FP32 units outrun the FP64 ones by ~70x.  A solver
+ * confirms a residual below its tolerance with the native FP64 operator.
+ * Errors as tm_apply_Mhat. */
+tm_status tm_apply_Mhat_dw(tm_ctx* ctx, tm_op op, void* out, const void* in, void* stream);
+
 /* The even pass of one Schur operator alone: out = M_ee(s)^-1 H_eo in, the even
  * sites' reconstruction term of eq:hQpm / eq:hQh (x_e = M_ee^-1 (b_e + kappa H_eo x_o)
  * for the full system).  op = TM_QHAT_PLUS / TM_QH (s = +) or TM_QHAT_MINUS /

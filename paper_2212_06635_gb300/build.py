@@ -16,7 +16,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libtm.so")
-SOURCES = ["dslash.cu", "dslash_heavy.cu", "dslash_staged.cu", "blas.cu", "gauge.cu", "ptc.cu", "force.cu", "rational.cu", "api.cu", "noalloc.cu", "mg.cu", "peak.cu"]
+SOURCES = ["dslash.cu", "dslash_heavy.cu", "dslash_staged.cu", "dslash_dw.cu", "blas.cu", "gauge.cu", "ptc.cu", "force.cu", "rational.cu", "api.cu", "noalloc.cu", "mg.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

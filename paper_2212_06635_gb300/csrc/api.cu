@@ -131,7 +131,7 @@ enum WsId {
     WS_B64 = 1, WS_X64, WS_R64, WS_AX64, WS_TE64, WS_MID64, WS_V64,
     WS_TE_S, WS_MID_S, WS_R_S, WS_P_S, WS_AP_S, WS_X_S,
     WS_STAGE_B, WS_STAGE_X, WS_STAGE_G, WS_APPLY_TE, WS_APPLY_MID, WS_STAGE_IO, WS_TUNE,
-    WS_FCG_Z,
+    WS_FCG_Z, WS_XDF,
     WS_MS_X = 100, WS_MS_P = 200, WS_MS_X64 = 300, WS_RAT = 400
 };
 
@@ -182,6 +182,8 @@ extern "C" tm_status tm_destroy(tm_ctx* c) {
         cudaFree(c->clovAP[q]); cudaFree(c->clovBP[q]); cudaFree(c->clovHP[q]); cudaFree(c->clovAeP[q]);
     }
     cudaFree(c->clovB64); cudaFree(c->clovH64);
+    cudaFree(c->gaugeDF[0]); cudaFree(c->gaugeDF[1]);
+    for (int k = 0; k < 3; ++k) cudaFree(c->clovDF[k]);
     cudaFree(c->partial); cudaFree(c->counter); cudaFree(c->ctl); cudaFree(c->ms); cudaFree(c->d_scal);
     cudaFreeHost(c->h_ctl); cudaFreeHost(c->h_ms); cudaFreeHost(c->h_scal);
     for (auto& kv : c->ws) cudaFree(kv.second.first);
@@ -321,10 +323,42 @@ static tm_status ensure_prec(tm_ctx* c, int P, cudaStream_t st) {
     return TM_OK;
 }
 
-static const void* gauge_ptr(const tm_ctx* c, int P, int par) { return P == P64 ? c->gauge64[par] : c->gaugeP[P][par]; }
-static const void* clovA_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovA64[1] : c->clovAP[P]; }
-static const void* clovB_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovB64 : c->clovBP[P]; }
-static const void* clovH_ptr(const tm_ctx* c, int P) { return P == P64 ? (const void*)c->clovH64 : c->clovHP[P]; }
+// double-word copies of the FP64 links and clover arrays (made when stale)
+static tm_status ensure_df(tm_ctx* c, cudaStream_t st) {
+    CKS(ensure_prec(c, P64, st));
+    const long vh = c->vh;
+    if (c->gaugeDF_gen != c->gauge_gen) {
+        for (int p = 0; p < 2; ++p) {
+            if (!c->gaugeDF[p]) CK(cudaMalloc(&c->gaugeDF[p], link_bytes_parity(PDF, vh)));
+            CK(launch_f64_to_df(c->gaugeDF[p], c->gauge64[p], 4 * 9 * vh, st));
+        }
+        c->gaugeDF_gen = c->gauge_gen;
+    }
+    if (c->clovDF_stamp != c->clover_stamp) {
+        const double* src[3] = {c->clovA64[1], c->clovB64, c->clovH64};
+        const int nreal[3] = {CLOV_ODD_REALS, CLOV_EVEN_LIGHT_REALS, CLOV_EVEN_HEAVY_REALS};
+        for (int k = 0; k < 3; ++k) {
+            if (k == 2 && !c->have_heavy) continue;
+            if (!c->clovDF[k]) CK(cudaMalloc(&c->clovDF[k], (size_t)8 * nreal[k] * vh));
+            CK(launch_f64_to_df(c->clovDF[k], src[k], (long)nreal[k] / 2 * vh, st));
+        }
+        c->clovDF_stamp = c->clover_stamp;
+    }
+    return TM_OK;
+}
+
+static const void* gauge_ptr(const tm_ctx* c, int P, int par) {
+    return P == P64 ? c->gauge64[par] : P == PDF ? c->gaugeDF[par] : c->gaugeP[P][par];
+}
+static const void* clovA_ptr(const tm_ctx* c, int P) {
+    return P == P64 ? (const void*)c->clovA64[1] : P == PDF ? c->clovDF[0] : c->clovAP[P];
+}
+static const void* clovB_ptr(const tm_ctx* c, int P) {
+    return P == P64 ? (const void*)c->clovB64 : P == PDF ? c->clovDF[1] : c->clovBP[P];
+}
+static const void* clovH_ptr(const tm_ctx* c, int P) {
+    return P == P64 ? (const void*)c->clovH64 : P == PDF ? c->clovDF[2] : c->clovHP[P];
+}
 
 // ---------------------------------------------------------------------------
 // operator application
@@ -338,7 +372,7 @@ static int pass_nblk(long vh, int nf, int kind, int staged) {
 // launch one pass in the variant the context chose for (P, NF, KIND)
 template <int P, int NF, int KIND, int NP>
 static cudaError_t launch_pass(int variant, const OpBatch<NP>& b, int nb, cudaStream_t st) {
-    if constexpr (P != P64) {
+    if constexpr (P != P64 && P != PDF) {
         if (variant) return launch_dslash_staged<P, NF, KIND, NP>(b, nb, st);
     }
     return launch_dslash<P, NF, KIND, NP>(b, nb, st);
@@ -348,7 +382,8 @@ static OpProb make_prob(const tm_ctx* c, int P, int nf, int kind, int sign, void
                         const void* loc, SolverCtl* ctl, bool fuse, double rho = 0.0) {
     OpProb p{};
     p.g = c->g;
-    p.nblk = pass_nblk(c->vh, nf, kind, c->variant[P][nf - 1][kind]);
+    // (the double-word passes run a thread per site and flavour)
+    p.nblk = P == PDF ? nblk((long)nf * c->vh, DSLASH_BS) : pass_nblk(c->vh, nf, kind, c->variant[P][nf - 1][kind]);
     p.bc_t = (float)c->params.bc_t;
     p.gauge[0] = gauge_ptr(c, P, 0);
     p.gauge[1] = gauge_ptr(c, P, 1);
@@ -380,12 +415,14 @@ static cudaError_t schur(const tm_ctx* c, int sign, void* out, const void* in, v
     b.p[0] = make_prob(c, P, NF, K1_EO_INV, sign, te, in, nullptr, ctl, false);
     b.blk_start[0] = 0;
     b.blk_start[1] = b.p[0].nblk;
-    cudaError_t e = launch_pass<P, NF, K1_EO_INV, 1>(c->variant[P][NF - 1][K1_EO_INV], b, b.p[0].nblk, st);
+    const int v1 = P == PDF ? 0 : c->variant[P][NF - 1][K1_EO_INV];
+    const int v2 = P == PDF ? 0 : c->variant[P][NF - 1][K2_OE_LOCAL];
+    cudaError_t e = launch_pass<P, NF, K1_EO_INV, 1>(v1, b, b.p[0].nblk, st);
     if (e != cudaSuccess) return e;
     b.fin = fin;
     b.p[0] = make_prob(c, P, NF, K2_OE_LOCAL, sign, out, te, in, ctl, fin != FIN_NONE, rho);
     b.blk_start[1] = b.p[0].nblk;
-    return launch_pass<P, NF, K2_OE_LOCAL, 1>(c->variant[P][NF - 1][K2_OE_LOCAL], b, b.p[0].nblk, st);
+    return launch_pass<P, NF, K2_OE_LOCAL, 1>(v2, b, b.p[0].nblk, st);
 }
 
 // signs of the two factors of a normal operator (first applied first)
@@ -462,6 +499,32 @@ extern "C" tm_status tm_apply_Mhat(tm_ctx* c, tm_op op, tm_prec prec, void* out,
         case TM_F16: return h ? apply_t<PF16, 2>(c, op, out, in, st) : apply_t<PF16, 1>(c, op, out, in, st);
     }
     return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown precision");
+}
+
+// op(in) in double-word arithmetic on native FP64 fields (out doubles as the
+// double-word result and is converted in place)
+template <int NF>
+static tm_status apply_dw_t(tm_ctx* c, tm_op op, void* out, const void* in, cudaStream_t st) {
+    const long n16 = 12 * NF * c->vh;
+    void* xdf = nullptr;
+    CKS(ensure_df(c, st));
+    CKS(ws_get(c, WS_XDF, spinor_bytes(PDF, 12 * NF, c->vh), &xdf));
+    CK(launch_f64_to_df(xdf, in, n16, st));
+    CKS(apply_t<PDF, NF>(c, op, out, xdf, st));
+    CK(launch_df_to_f64(out, out, n16, st));
+    return TM_OK;
+}
+
+extern "C" tm_status tm_apply_Mhat_dw(tm_ctx* c, tm_op op, void* out, const void* in, void* stream) {
+    if (!c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: bad pointers");
+    if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: fields must be 16-byte aligned");
+    if (op < TM_QHAT_PLUS || op > TM_WHAT_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: unknown op %d", (int)op);
+    CK(cudaSetDevice(c->device));
+    const cudaStream_t st = S(stream);
+    CKS(ensure_prec(c, P64, st));
+    if (nflav(op) == 2 && !c->have_heavy)
+        return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: heavy operator needs mubar or epsbar in tm_clover_compute");
+    return nflav(op) == 2 ? apply_dw_t<2>(c, op, out, in, st) : apply_dw_t<1>(c, op, out, in, st);
 }
 
 // the even pass alone: out (even sites) = M_ee(sign)^-1 H_eo in (odd sites)
@@ -843,14 +906,28 @@ static tm_status get_ctl(tm_ctx* c, cudaStream_t st) {
     return TM_OK;
 }
 
-// r64 = b64 - (A + shift) x64, returns ||r64||^2
-template <int NF>
 // r = b - (A + shift) x and rr = ||r||^2 in FP64.  x_zero: x is known to be zero,
-// so A x = 0 without applying the operator (a zero initial guess).
+// so A x = 0 without applying the operator (a zero initial guess).  dw: A x in
+// double-word arithmetic (x and the result rounded to a 48-bit significand on the
+// way in and out; mid64, te64 and ax64 serve as double-word scratch), for the
+// reliable updates inside a mixed-precision solve; otherwise native FP64.
+template <int NF>
 static tm_status true_residual(tm_ctx* c, tm_op op, double shift, void* x64, void* b64, void* r64, void* ax64,
-                               void* mid64, void* te64, cudaStream_t st, double* rr, bool x_zero = false) {
-    if (x_zero) CK(cudaMemsetAsync(ax64, 0, spinor_bytes(P64, 12 * NF, c->vh), st));
-    else CK((normal_op<P64, NF>(c, op, ax64, x64, mid64, te64, st, nullptr, FIN_NONE)));
+                               void* mid64, void* te64, cudaStream_t st, double* rr, bool x_zero = false,
+                               bool dw = false) {
+    const long n16 = 12 * NF * c->vh;   // 16-byte elements of a field
+    if (x_zero) {
+        CK(cudaMemsetAsync(ax64, 0, spinor_bytes(P64, 12 * NF, c->vh), st));
+    } else if (dw) {
+        void* xdf = nullptr;
+        CKS(ensure_df(c, st));
+        CKS(ws_get(c, WS_XDF, spinor_bytes(PDF, 12 * NF, c->vh), &xdf));
+        CK(launch_f64_to_df(xdf, x64, n16, st));
+        CK((normal_op<PDF, NF>(c, op, ax64, xdf, mid64, te64, st, nullptr, FIN_NONE)));
+        CK(launch_df_to_f64(ax64, ax64, n16, st));
+    } else {
+        CK((normal_op<P64, NF>(c, op, ax64, x64, mid64, te64, st, nullptr, FIN_NONE)));
+    }
     c->h_ctl->shift = shift;
     CK(cudaMemcpyAsync(&c->ctl->shift, &c->h_ctl->shift, sizeof(double), cudaMemcpyHostToDevice, st));
     CK((launch_residual64<12 * NF, 1>(vb1(c, r64, b64, ax64, x64, c->d_scal), nblk(c->vh, BLAS_BS), st)));
@@ -940,8 +1017,11 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
     double rr = 0;
     bool x0 = false;
     CKS(is_zero64<NF>(c, x64, st, &x0));
-    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, x0));
+    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, x0, PS != P64));
     const double target = tol * tol * bb;
+    // an initial guess already within the tolerance is confirmed in FP64
+    if (PS != P64 && !x0 && rr <= target)
+        CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
     tm_status status = TM_OK;
     cudaGraphExec_t gexec = nullptr;
     if (rr > target) {
@@ -987,8 +1067,12 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
                 CK((launch_add_to64<P32, NC, 1>(vb1(c, x64, xs), nb, st)));
                 CK(cudaMemsetAsync(xs, 0, spinor_bytes(P32, NC, vh), st));
             }
-            CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
+            CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, false, PS != P64));
             info->reliable_updates += 1;
+            // a double-word residual below the target is confirmed in FP64 (the
+            // returned true residual is always an FP64 one)
+            if (PS != P64 && rr <= target)
+                CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
             if (rr <= target) break;
             if (h.flag == CTL_MAXITER || h.iter >= maxiter || !std::isfinite(rr)) {
                 status = std::isfinite(rr) ? TM_ERR_NOT_CONVERGED : TM_ERR_BREAKDOWN;
@@ -1694,7 +1778,10 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
             const int saved_flag = h.flag;
             const double rr_old = h.rr_old;
             const int iters = h.iter;
-            CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
+            CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q], false,
+                                 PS != P64));
+            if (PS != P64 && rr[q] <= tol * tol * bb[q])   // confirmed in FP64
+                CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
             infos[q].reliable_updates += 1;
             // true_residual overwrote h.shift only; restore the control word
             h.flag = saved_flag;
@@ -2329,7 +2416,9 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
         }
         if (status != TM_OK) break;
         CK((launch_add_to64<P32, 12, 1>(vb1(c, x64, xs), nb, st)));
-        CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
+        CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr, false, true));
+        if (rr <= target)   // confirmed in FP64
+            CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
         info->reliable_updates += 1;
         if (its >= maxiter && rr > target) { status = TM_ERR_NOT_CONVERGED; break; }
     }

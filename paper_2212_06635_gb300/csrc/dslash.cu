@@ -195,6 +195,7 @@ cudaError_t launch_dslash(const OpBatch<NP>& b, int nblocks, cudaStream_t st) {
     TM_INST(P, 1, K1_EO_INV, 1) TM_INST(P, 1, K2_OE_LOCAL, 1) TM_INST(P, 2, K2_OE_LOCAL, 1) \
     TM_INST(P, 1, K1_EO_INV, MAXP) TM_INST(P, 1, K2_OE_LOCAL, MAXP)
 TM_INST_P(P64)
+// (the double-word passes: dslash_dw.cu)
 TM_INST_P(P32)
 TM_INST_P(PB16)
 TM_INST_P(PF16)

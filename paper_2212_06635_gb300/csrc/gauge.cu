@@ -340,6 +340,35 @@ cudaError_t launch_clover_unpack(double* out, const double* A, long vh, cudaStre
     return cudaGetLastError();
 }
 
+// FP64 arrays (a double2 per two reals: links, clover blocks, spinors) <->
+// double-word arrays (a float4 (h, l, h, l) per two reals), n 16-byte elements;
+// in place is allowed (each thread reads and writes only its own element)
+__global__ void k_f64_to_df(float4* dst, const double2* src, long n) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const double2 v = src[e];
+    const df x(v.x), y(v.y);
+    dst[e] = make_float4(x.h, x.l, y.h, y.l);
+}
+__global__ void k_df_to_f64(double2* dst, const float4* src, long n) {
+    const long e = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const float4 q = src[e];
+    dst[e] = make_double2((double)df(q.x, q.y), (double)df(q.z, q.w));
+}
+cudaError_t launch_f64_to_df(void* dst, const void* src, long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_f64_to_df<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<float4*>(dst),
+                                                              reinterpret_cast<const double2*>(src), n);
+    return cudaGetLastError();
+}
+cudaError_t launch_df_to_f64(void* dst, const void* src, long n, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    k_df_to_f64<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(reinterpret_cast<double2*>(dst),
+                                                              reinterpret_cast<const float4*>(src), n);
+    return cudaGetLastError();
+}
+
 template cudaError_t launch_links_from64<P32>(void*, const void*, long, cudaStream_t);
 template cudaError_t launch_links_from64<PB16>(void*, const void*, long, cudaStream_t);
 template cudaError_t launch_links_from64<PF16>(void*, const void*, long, cudaStream_t);

@@ -37,6 +37,12 @@ struct tm_ctx {
     void* clovBP[4] = {};
     void* clovHP[4] = {};
     long clovP_stamp[4] = {0, 0, 0, 0};
+    // double-word copies of the FP64 links and clover arrays (odd A, even light,
+    // even heavy) for the reliable updates of the mixed-precision solvers
+    void* gaugeDF[2] = {nullptr, nullptr};
+    long gaugeDF_gen = 0;
+    void* clovDF[3] = {};
+    long clovDF_stamp = 0;
     // even-site A in a storage precision, made only for the full operator (multigrid)
     void* clovAeP[4] = {};
     long clovAeP_stamp[4] = {0, 0, 0, 0};

@@ -10,6 +10,7 @@
 
 #include "../../include/tm.h"
 #include "fastdiv.h"
+#include "df64.h"
 
 namespace tmk {
 
@@ -57,15 +58,20 @@ template <typename R> __host__ __device__ __forceinline__ R norm2(cpx<R> a) { re
 //   clover per parity, a flat list of reals (multiples of 8) in W-wide vectors.
 // ---------------------------------------------------------------------------
 enum Prec { P64 = 0, P32 = 1, PB16 = 2, PF16 = 3 };
+// Kernel-internal precision of the reliable updates: FP64 storage layouts and
+// sizes, double-word arithmetic (df64.h).  Links, clover blocks and spinors are
+// held as (hi, lo) FP32 pairs, a float4 per two reals (the FP64 double2 slot).
+constexpr int PDF = 4;
 
 template <int P> struct PT;
 template <> struct PT<P64> { using R = double; static constexpr int W = 2; static constexpr int ESZ = 8; };
 template <> struct PT<P32> { using R = float;  static constexpr int W = 4; static constexpr int ESZ = 4; };
 template <> struct PT<PB16> { using R = float; static constexpr int W = 8; static constexpr int ESZ = 2; };
 template <> struct PT<PF16> { using R = float; static constexpr int W = 8; static constexpr int ESZ = 2; };
+template <> struct PT<PDF> { using R = df; static constexpr int W = 2; static constexpr int ESZ = 8; };
 
-__host__ __device__ inline int prec_esz(int p) { return p == P64 ? 8 : (p == P32 ? 4 : 2); }
-__host__ __device__ inline int prec_w(int p) { return p == P64 ? 2 : (p == P32 ? 4 : 8); }
+__host__ __device__ inline int prec_esz(int p) { return (p == P64 || p == PDF) ? 8 : (p == P32 ? 4 : 2); }
+__host__ __device__ inline int prec_w(int p) { return (p == P64 || p == PDF) ? 2 : (p == P32 ? 4 : 8); }
 
 // bytes of a native spinor field of nc complex components per site
 __host__ __device__ inline size_t spinor_bytes(int p, int nc, long vh) {
@@ -122,6 +128,9 @@ __device__ __forceinline__ void load_reals(const void* base, long vh, long i, in
         if constexpr (P == P64) {
             double2 q = __ldg(reinterpret_cast<const double2*>(base) + e);
             dst[2 * v] = q.x; dst[2 * v + 1] = q.y;
+        } else if constexpr (P == PDF) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(base) + e);
+            dst[2 * v] = df(q.x, q.y); dst[2 * v + 1] = df(q.z, q.w);
         } else if constexpr (P == P32) {
             float4 q = __ldg(reinterpret_cast<const float4*>(base) + e);
             dst[4 * v] = q.x; dst[4 * v + 1] = q.y; dst[4 * v + 2] = q.z; dst[4 * v + 3] = q.w;
@@ -148,6 +157,8 @@ __device__ __forceinline__ void store_reals(void* base, long vh, long i, int off
         const long e = (long)(v0 + v) * vh + i;
         if constexpr (P == P64) {
             reinterpret_cast<double2*>(base)[e] = make_double2(src[2 * v], src[2 * v + 1]);
+        } else if constexpr (P == PDF) {
+            reinterpret_cast<float4*>(base)[e] = make_float4(src[2 * v].h, src[2 * v].l, src[2 * v + 1].h, src[2 * v + 1].l);
         } else if constexpr (P == P32) {
             reinterpret_cast<float4*>(base)[e] =
                 make_float4(src[4 * v], src[4 * v + 1], src[4 * v + 2], src[4 * v + 3]);
@@ -238,6 +249,9 @@ __device__ __forceinline__ void load_link(const void* base, long vh, int mu, lon
         if constexpr (P == P64) {
             double2 q = __ldg(reinterpret_cast<const double2*>(base) + e);
             u[k] = C(q.x, q.y);
+        } else if constexpr (P == PDF) {
+            float4 q = __ldg(reinterpret_cast<const float4*>(base) + e);
+            u[k] = C(df(q.x, q.y), df(q.z, q.w));
         } else if constexpr (P == P32) {
             float2 q = __ldg(reinterpret_cast<const float2*>(base) + e);
             u[k] = C(q.x, q.y);

@@ -214,5 +214,7 @@ template <int P>
 cudaError_t launch_links_from64(void* dst, const void* src64, long vh, cudaStream_t st);
 template <int P>
 cudaError_t launch_clover_from64(void* dst, const double* src, long vh, int nreal, cudaStream_t st);
+cudaError_t launch_f64_to_df(void* dst, const void* src, long n, cudaStream_t st);
+cudaError_t launch_df_to_f64(void* dst, const void* src, long n, cudaStream_t st);
 
 }  // namespace tmk

@@ -83,6 +83,41 @@ def stencil_passes(dims, prec, nf, reps, variant="direct", quiet=False):
         tm.tm_destroy(ctx)
 
 
+def double_word(dims, nf, reps, quiet=False):
+    """CUDA-event time of the normal operator (M_hat^dag M_hat light, Q_hat_h
+    Q_hat_h^dag heavy) on native FP64 fields: native FP64 arithmetic
+    (tm_apply_Mhat, TM_F64) against double-word arithmetic (tm_apply_Mhat_dw,
+    conversions in and out included).  Returns (FP64 ms, double-word ms)."""
+    import torch
+    from paper_2212_06635_gb300 import tm
+    from synth import fields as F
+    ctx = _ctx(tm, dims, nf == 2)
+    try:
+        src = torch.from_numpy(F.odd_spinor(dims, 2002, nf).view(np.float64).copy()).cuda()
+        a = torch.empty(tm.tm_field_bytes(ctx, 0, nf), dtype=torch.uint8, device="cuda")
+        o = torch.empty_like(a)
+        tm.tm_field_import(ctx, 0, nf, a, src)
+        op = tm.TM_QH_SQ if nf == 2 else tm.TM_MDAGM
+        res = []
+        for f in (lambda: tm.tm_apply_Mhat(ctx, op, 0, o, a), lambda: tm.tm_apply_Mhat_dw(ctx, op, o, a)):
+            f()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                f()
+            e1.record()
+            torch.cuda.synchronize()
+            res.append(e0.elapsed_time(e1) / max(reps, 1))
+        if not quiet:
+            print(f"dims {dims} nf {nf} normal operator on FP64 fields: native FP64 {res[0] * 1e3:.1f} us, "
+                  f"double-word {res[1] * 1e3:.1f} us ({res[0] / res[1]:.2f}x)")
+        return tuple(res)
+    finally:
+        tm.tm_destroy(ctx)
+
+
 def force_bytes(dims, prec, nf, n):
     """Algorithmic bytes of one tm_force_outer launch: every field read once
     (2 n fields on V sites), the FP32 links once (12 reals per link), the FP64
@@ -215,10 +250,11 @@ def ptc_fcg(dims, iters, quiet=False):
         tm.tm_destroy(ctx)
 
 
-def cg_solve(dims, prec, quiet=False):
-    """One CG solve of M_hat^dag M_hat to true rel. res. 1e-10 with the given
-    sloppy storage (FP64: plain FP64 CG): the launch sequence of the solver's
-    stencil and BLAS-1 kernels."""
+def cg_solve(dims, prec, quiet=False, delta=0.0, solves=1):
+    """CG solves of M_hat^dag M_hat to true rel. res. 1e-10 with the given sloppy
+    storage (FP64: plain FP64 CG) and reliable-update threshold (0: the library's
+    default), from a zero guess: the launch sequence of the solver's stencil and
+    BLAS-1 kernels.  Returns the last solve's info."""
     import torch
     from paper_2212_06635_gb300 import tm
     from synth import fields as F
@@ -227,11 +263,14 @@ def cg_solve(dims, prec, quiet=False):
         if prec != 0:
             tm.tm_autotune(ctx, prec, 1)
         bd = torch.from_numpy(F.odd_spinor(dims, 2001).view(np.float64).copy()).cuda()
-        x = torch.zeros_like(bd)
-        info = tm.tm_solve_cg(ctx, tm.TM_MDAGM, tm.solve_params(tol=1e-10, sloppy=prec), x, bd, check=False)
-        if not quiet:
-            print(f"dims {dims} CG sloppy {prec}: {info.iters} iterations, {info.seconds:.4f} s, "
-                  f"residual {info.true_rel_res:.2e}")
+        for _ in range(solves):
+            x = torch.zeros_like(bd)
+            info = tm.tm_solve_cg(ctx, tm.TM_MDAGM, tm.solve_params(tol=1e-10, sloppy=prec, delta=delta), x, bd,
+                                  check=False)
+            if not quiet:
+                print(f"dims {dims} CG sloppy {prec} delta {delta}: {info.iters} iterations, "
+                      f"{info.reliable_updates} reliable updates, {info.seconds:.4f} s, "
+                      f"residual {info.true_rel_res:.2e}")
         return info
     finally:
         tm.tm_destroy(ctx)
@@ -344,6 +383,8 @@ def main():
     ap.add_argument("--force", type=int, default=0, metavar="NPAIRS")
     ap.add_argument("--solve", action="store_true")
     ap.add_argument("--multishift", action="store_true")
+    ap.add_argument("--delta", type=float, default=0.0, help="--solve: reliable-update threshold (0: default)")
+    ap.add_argument("--solves", type=int, default=1, help="--solve: solves in a row (the first one warms up)")
     ap.add_argument("--mg", type=int, default=0, metavar="ITERS",
                     help="multigrid setup, then ITERS iterations of multigrid-preconditioned GCR")
     ap.add_argument("--setup", type=int, default=100, help="--mg: minimal-residual steps per near-null vector")
@@ -351,6 +392,8 @@ def main():
                     help="the uneven batch of 24 light solves, batched or one after another")
     ap.add_argument("--chunk", type=int, default=16, help="--batch: iterations between host checks")
     ap.add_argument("--fma", action="store_true", help="measured FP64 and FP32 FMA rates")
+    ap.add_argument("--dw", action="store_true",
+                    help="normal operator on FP64 fields: native FP64 against double-word arithmetic")
     a = ap.parse_args()
     dims = tuple(a.dims)
     prec = PRECS[a.prec]
@@ -364,13 +407,15 @@ def main():
     elif a.force:
         force_outer(dims, prec, nf, a.force, a.reps)
     elif a.solve:
-        cg_solve(dims, prec)
+        cg_solve(dims, prec, delta=a.delta, solves=a.solves)
     elif a.multishift:
         multishift(dims, prec)
     elif a.mg:
         mg_solve(dims, setup=a.setup, maxiter=a.mg)
     elif a.batch:
         batch_solve(sequential=a.batch == "sequential", chunk=a.chunk)
+    elif a.dw:
+        double_word(dims, nf, a.reps)
     elif a.fma:
         from paper_2212_06635_gb300 import tm
         for p, name in ((0, "FP64"), (1, "FP32")):

@@ -81,6 +81,7 @@ _sigs = {
     "tm_field_import": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_field_export": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
     "tm_apply_Mhat": [_vp, ct.c_int, ct.c_int, _vp, _vp, _vp],
+    "tm_apply_Mhat_dw": [_vp, ct.c_int, _vp, _vp, _vp],
     "tm_solve_cg": [_vp, ct.c_int, ct.POINTER(tm_solve_params), _vp, _vp, ct.POINTER(tm_solve_info), _vp],
     "tm_solve_multishift": [_vp, ct.c_int, ct.c_int, ct.POINTER(ct.c_double), ct.POINTER(_vp), _vp,
                             ct.POINTER(tm_solve_params), ct.POINTER(tm_solve_info), _vp],
@@ -234,6 +235,11 @@ def tm_field_norm2_noalloc(ctx, prec, nflavour, field, result, stream=None):
 
 def tm_apply_Mhat(ctx, op, prec, out, inp, stream=None):
     _check(lib.tm_apply_Mhat(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
+
+
+def tm_apply_Mhat_dw(ctx, op, out, inp, stream=None):
+    """out = op(inp) on native FP64 fields in double-word arithmetic."""
+    _check(lib.tm_apply_Mhat_dw(ctx, int(op), ptr(out), ptr(inp), _stream(stream)))
 
 
 def tm_apply_even(ctx, op, prec, out, inp, stream=None):

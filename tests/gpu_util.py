@@ -8,6 +8,11 @@ import numpy as np
 # stored BF16 field alone carries about 2e-3 relative error, so a normal operator
 # (two applications with a stored BF16 intermediate) gets twice the bound.
 PREC_TOL = {0: 1e-13, 1: 1e-6, 2: 3e-3, 3: 3e-3}
+# double-word arithmetic (tm_apply_Mhat_dw): unit roundoff 2^-47 of the double-word
+# sum, the input and output rounded to 48 bits, a few hundred operations per
+# output element over the two passes of a Schur operator: 1e-13 per application,
+# 2e-13 for a normal operator
+DW_TOL = 1e-13
 
 
 def tol(prec, napply=1):
@@ -63,6 +68,20 @@ class Lat:
         self.tm.tm_apply_Mhat(self.ctx, op, prec, o, a)
         out = src.clone()
         self.tm.tm_field_export(self.ctx, prec, nf, out, o)
+        import torch
+        torch.cuda.synchronize()
+        return from_dev(out, psi.shape)
+
+    def apply_dw(self, op, psi):
+        """op applied in double-word arithmetic (tm_apply_Mhat_dw) on FP64 fields."""
+        nf = 1 if psi.ndim == 3 else 2
+        src = to_dev(psi)
+        a = self.native(0, nf)
+        o = self.native(0, nf)
+        self.tm.tm_field_import(self.ctx, 0, nf, a, src)
+        self.tm.tm_apply_Mhat_dw(self.ctx, op, o, a)
+        out = src.clone()
+        self.tm.tm_field_export(self.ctx, 0, nf, out, o)
         import torch
         torch.cuda.synchronize()
         return from_dev(out, psi.shape)

@@ -44,6 +44,8 @@ def test_null_arguments_rejected(tm):
     assert tm.lib.tm_destroy(None) == tm.TM_OK
     v = ct.c_double()
     assert tm.lib.tm_gauge_id(None, ct.byref(v)) == tm.TM_ERR_ARG
+    assert tm.lib.tm_apply_Mhat_dw(None, 2, None, None, None) == tm.TM_ERR_ARG
+    assert "bad pointers" in tm.tm_last_error()
 
 
 def test_force_outer_host_checks(tm):

@@ -6,7 +6,7 @@ import pytest
 
 from oracle import dirac as D
 from synth import fields as F
-from tests.gpu_util import Lat, rel, tol
+from tests.gpu_util import DW_TOL, Lat, rel, tol
 
 pytestmark = pytest.mark.gpu
 
@@ -59,6 +59,42 @@ def test_heavy_schur_operators(setup, prec):
                          (tm.TM_QH_SQ, op.heavy_sq(psi), 2)):
         got = lat.apply(code, prec, psi)
         assert rel(got, ref) < tol(prec, n), (code, rel(got, ref))
+
+
+def test_double_word_operators(setup):
+    """tm_apply_Mhat_dw (the reliable updates' operator) against the oracle and
+    against the native FP64 operator, light and heavy, single and normal."""
+    dims, op, lat = setup
+    tm = lat.tm
+    psi = F.odd_spinor(dims, 7)
+    psih = F.odd_spinor(dims, 8, 2)
+    for code, ref, x, n in ((tm.TM_QHAT_PLUS, op.Qhat(psi, +1), psi, 1), (tm.TM_QHAT_MINUS, op.Qhat(psi, -1), psi, 1),
+                            (tm.TM_MDAGM, op.MdagM(psi), psi, 2), (tm.TM_QPQM, op.QpQm(psi), psi, 2),
+                            (tm.TM_QH, op.Qhat_heavy(psih, +1), psih, 1),
+                            (tm.TM_QH_DAG, op.Qhat_heavy(psih, -1), psih, 1),
+                            (tm.TM_QH_SQ, op.heavy_sq(psih), psih, 2)):
+        got = lat.apply_dw(code, x)
+        assert rel(got, ref) < n * DW_TOL, (code, rel(got, ref))
+        assert rel(got, lat.apply(code, 0, x)) < n * DW_TOL, code
+
+
+def test_double_word_copies_follow_the_gauge_field():
+    """The double-word links and clover blocks are remade after a new gauge field
+    and clover term."""
+    dims = (4, 4, 4, 6)
+    u1 = F.gauge_field(dims, 31)
+    u2 = F.gauge_field(dims, 32)
+    lat = Lat(u1, dims, KAPPA, CSW, mu=MU)
+    try:
+        psi = F.odd_spinor(dims, 33)
+        op1 = D.TwistedMassClover(u1, dims, KAPPA, CSW, mu=MU)
+        assert rel(lat.apply_dw(lat.tm.TM_MDAGM, psi), op1.MdagM(psi)) < 2 * DW_TOL
+        lat.tm.tm_gauge_load(lat.ctx, np.ascontiguousarray(u2), 2.0)
+        lat.tm.tm_clover_compute(lat.ctx, KAPPA, CSW, mu=2 * MU)
+        op2 = D.TwistedMassClover(u2, dims, KAPPA, CSW, mu=2 * MU)
+        assert rel(lat.apply_dw(lat.tm.TM_MDAGM, psi), op2.MdagM(psi)) < 2 * DW_TOL
+    finally:
+        lat.close()
 
 
 def test_periodic_time_boundary():
