@@ -331,7 +331,12 @@ def run_ours(args, rank, world, local_rank):
     try:
         tm.tm_gauge_load(ctx, u, 1.0)
         tm.tm_clover_compute(ctx, W.kappa, W.csw, mu=W.mu, bc_t=W.bc_t)
-        tuning = tm.tm_autotune(ctx, prec, 1)
+        if args.variant == "auto":
+            tuning = tm.tm_autotune(ctx, prec, 1)
+        else:   # a fixed stencil variant (a profiler run times kernels unlike a plain one)
+            v = 1 if args.variant == "staged" else 0
+            tm.tm_set_tuning(ctx, prec, 1, v, v)
+            tuning = (v, v)
         bd = torch.from_numpy(b.view(np.float64).copy()).to(dev)
         nbytes = tm.tm_field_bytes(ctx, prec, 1)
         fin = torch.empty(nbytes, dtype=torch.uint8, device=dev)
@@ -846,6 +851,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--storage", default="f16", choices=["f16", "bf16", "f32"])
+    ap.add_argument("--variant", default="auto", choices=["auto", "direct", "staged"],
+                    help="stencil variant of the step (auto: the autotuner's choice)")
     ap.add_argument("--maxiter", type=int, default=60000)
     ap.add_argument("--no-fp64", action="store_true", help="skip the FP64 CG time-to-solution leg")
     ap.add_argument("--no-solve", action="store_true", help="skip both time-to-solution legs")
