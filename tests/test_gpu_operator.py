@@ -260,5 +260,9 @@ def test_mass_preconditioned_W_hat(prec):
             assert rel(lat.apply(tm.TM_WHAT_PLUS, prec, psi), wp) < tol(prec)
             assert rel(lat.apply(tm.TM_WHAT_MINUS, prec, psi), wm) < tol(prec)
             assert rel(lat.apply(tm.TM_WHAT_SQ, prec, psi), wsq) < tol(prec, 2)
+            if prec == 0:   # and the double-word form of the reliable updates
+                assert rel(lat.apply_dw(tm.TM_WHAT_PLUS, psi), wp) < DW_TOL
+                assert rel(lat.apply_dw(tm.TM_WHAT_MINUS, psi), wm) < DW_TOL
+                assert rel(lat.apply_dw(tm.TM_WHAT_SQ, psi), wsq) < 2 * DW_TOL
     finally:
         lat.close()

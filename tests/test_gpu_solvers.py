@@ -73,6 +73,36 @@ def test_qpqm_and_host_pointers_and_initial_guess():
         lat.close()
 
 
+@pytest.mark.parametrize("nf", [1, 2], ids=["light", "heavy"])
+def test_converged_initial_guess_returns_fp64_residual(nf):
+    """A mixed solve started from a solution: the double-word initial residual
+    is below the tolerance, the library confirms it with the FP64 operator and
+    returns without iterating; the returned residual is the FP64 one (checked
+    against the oracle's)."""
+    dims = (6, 4, 4, 6)
+    if nf == 1:
+        op, lat = _lat(dims, 1250)
+        A, b = op.MdagM, F.odd_spinor(dims, 2250)
+    else:
+        op, lat = _lat(dims, 1251, mubar=0.1246, epsbar=0.1350)
+        A, b = op.heavy_sq, F.odd_spinor(dims, 2251, 2)
+    tm = lat.tm
+    code = tm.TM_MDAGM if nf == 1 else tm.TM_QH_SQ
+    try:
+        x = to_dev(np.zeros_like(b))
+        sp = tm.solve_params(tol=1e-10, sloppy=tm.TM_F16)
+        tm.tm_solve_cg(lat.ctx, code, sp, x, to_dev(b))
+        xs = from_dev(x, b.shape)
+        res = S.rel_residual(A, xs, b)
+        assert res <= 1.05e-10
+        info = tm.tm_solve_cg(lat.ctx, code, sp, x, to_dev(b))
+        assert info.status == 0 and info.iters == 0 and info.reliable_updates == 0
+        assert abs(info.true_rel_res - res) <= 1e-3 * res
+        assert rel(from_dev(x, b.shape), xs) == 0.0
+    finally:
+        lat.close()
+
+
 def test_heavy_cg():
     dims = (4, 4, 4, 8)
     op, lat = _lat(dims, 1300, kappa=0.14, mu=0.0, mubar=0.1246, epsbar=0.135)
