@@ -1211,8 +1211,16 @@ static tm_status multishift_core(tm_ctx* c, tm_op op, int ns, const double* sh_s
         return fail(std::isfinite(bb) ? TM_ERR_ARG : TM_ERR_BREAKDOWN,
                     "multishift: right-hand side must be finite and non-zero");
     CK((launch_convert<PS, P64, NC, 1>(vb1(c, rs, b64), nb, st)));
-    // the sloppy multishift stops each shift near the precision floor of PS
-    const double floor_tol = PS == P64 ? 0.0 : (PS == P32 ? 1e-6 : 2e-4);
+    // The sloppy multishift stops each shift when its recursively updated residual
+    // falls below floor_tol; the shift-by-shift refinement takes it to sp->tol.
+    // Swept on the heavy doublet at 24^3x48 (12 shifts, time of the whole solve
+    // with refinement): FP32 1e-6 / 1e-7 / 1e-8 / 1e-9 / 1e-10 -> 0.721 / 0.631 /
+    // 0.594 / 0.611 / 0.634 s; 16-bit 2e-4 / 5e-5 / 1e-5 / 1e-6 -> 0.972 / 0.936 /
+    // 0.870 / 0.892 s.  Below the storage's own precision the sloppy solutions
+    // still improve (the reductions are FP64), and a refinement iteration costs
+    // about half a multishift one, until the extra multishift iterations stop
+    // paying.
+    const double floor_tol = PS == P64 ? 0.0 : (PS == P32 ? 1e-8 : 1e-5);
     const double ms_tol = std::max(sp->tol, floor_tol);
     MsCtl& m = *c->h_ms;
     std::memset(&m, 0, sizeof(MsCtl));
