@@ -105,7 +105,8 @@ typedef struct {
 
 typedef struct {
     int iters;            /* Krylov iterations */
-    int reliable_updates; /* FP64 true-residual recomputations */
+    int reliable_updates; /* true-residual recomputations (double-word arithmetic
+                             in the mixed solvers, FP64 in plain FP64 CG) */
     int status;           /* tm_status of this solve */
     double true_rel_res;  /* FP64 ||b - A x|| / ||b|| of the returned x */
     double seconds;       /* wall time of the call */
@@ -205,8 +206,10 @@ tm_status tm_apply_Mhat_dw(tm_ctx* ctx, tm_op op, void* out, const void* in, voi
 tm_status tm_apply_even(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in, void* stream);
 
 /* Solve A x = b, A = TM_MDAGM, TM_QPQM, TM_QH_SQ or TM_WHAT_SQ, by CG (sloppy = TM_F64) or by
- * mixed-precision CG with reliable updates (Sec. 4.1).  x, b canonical FP64, host
- * or device pointers; x is the initial guess on entry (zero it for none). */
+ * mixed-precision CG with reliable updates (Sec. 4.1; the true residuals between
+ * updates in double-word arithmetic, see tm_apply_Mhat_dw, a residual below
+ * the tolerance confirmed in FP64).  x, b canonical FP64, host or device
+ * pointers; x is the initial guess on entry (zero it for none). */
 tm_status tm_solve_cg(tm_ctx* ctx, tm_op op, const tm_solve_params* sp, double* x,
                       const double* b, tm_solve_info* info, void* stream);
 
@@ -365,8 +368,10 @@ tm_status tm_ptc_save(const tm_ptc* net, const char* path);
 tm_status tm_ptc_load(tm_ptc* net, const char* path);
 
 /* Flexible CG (truncation 1) on A = TM_MDAGM or TM_QPQM, preconditioned by net;
- * FP32 vectors and operator, BF16 network, FP64 reliable updates (sp->delta)
- * restarting the recursion; stops at FP64 true relative residual sp->tol.
+ * FP32 vectors and operator, BF16 network; reliable updates (sp->delta) in
+ * double-word arithmetic (tm_apply_Mhat_dw) restart the recursion; stops at
+ * FP64 true relative residual sp->tol (a residual below it is confirmed with the
+ * FP64 operator).
  * x, b canonical FP64 (host or device); sp->sloppy is ignored. */
 tm_status tm_solve_fcg(tm_ctx* ctx, tm_op op, tm_ptc* net, const tm_solve_params* sp, double* x,
                        const double* b, tm_solve_info* info, void* stream);
