@@ -968,7 +968,8 @@ static cudaError_t cg_iteration(tm_ctx* c, tm_op op, void* xs, void* p, void* r,
 // PS == P64: plain FP64 CG.  Otherwise mixed precision with reliable updates:
 // the iteration runs in PS storage / FP32 arithmetic with x accumulated in FP32;
 // whenever ||r|| has dropped by delta since the last true residual, x is folded
-// into the FP64 solution and r is recomputed as b - A x in FP64.
+// into the FP64 solution and r = b - A x is recomputed in double-word arithmetic
+// (true_residual); a residual below the tolerance is confirmed in FP64.
 template <int PS, int NF>
 static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_params* sp, void* x64, void* b64,
                             tm_solve_info* info, cudaStream_t st) {
@@ -1062,7 +1063,7 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
             CKS(get_ctl(c, st));
             if (h.flag == CTL_RUN) continue;
             if (h.flag == CTL_BREAKDOWN) { status = TM_ERR_BREAKDOWN; break; }
-            // reliable update / convergence check in FP64
+            // reliable update / convergence check
             if (PS != P64) {
                 CK((launch_add_to64<P32, NC, 1>(vb1(c, x64, xs), nb, st)));
                 CK(cudaMemsetAsync(xs, 0, spinor_bytes(P32, NC, vh), st));
@@ -2330,7 +2331,8 @@ extern "C" tm_status tm_ptc_load(tm_ptc* n, const char* path) {
 //   alpha = <p_k, r_k> / <p_k, q_k>;  x += alpha p_k;  r -= alpha q_k.
 // Vectors FP32, operator FP32, network BF16; every time the iterated residual has
 // dropped by `delta` the solution is folded into FP64 and r = b - A x is
-// recomputed with the FP64 operator (reliable update), restarting the recursion.
+// recomputed in double-word arithmetic (reliable update; FP64 once it is below
+// the tolerance), restarting the recursion.
 // ---------------------------------------------------------------------------
 extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve_params* sp, double* x,
                                   const double* b, tm_solve_info* info, void* stream) {
@@ -2388,7 +2390,7 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
     tm_status status = TM_OK;
     int its = 0;
     while (rr > target && bb > 0) {
-        // (re)start from the FP64 residual
+        // (re)start from the recomputed residual
         CK((launch_convert<P32, P64, 12, 1>(vb1(c, rs, r64), nb, st)));
         CK(cudaMemsetAsync(xs, 0, s32, st));
         const double rr_start = rr;
