@@ -14,7 +14,8 @@ residual 1e-10 of the chosen form (mixed-precision CG) and of plain FP64 CG on
 the same GPU.
 
 Before that headline line, one JSON line holds the records of the other
-workloads: the heavy-doublet multishift at 24^3x48, the uneven batch, the force
+workloads: the reliable updates' operator (native FP64 against double-word
+arithmetic) at 32^3x64, the heavy-doublet multishift at 24^3x48, the uneven batch, the force
 outer products, the rational correction term, the two-level multigrid of the
 full operator at 48^3x96 against the even-odd mixed CG route, and the PTC
 network trained on 2048 solver-generated pairs from 8 configurations at
@@ -22,7 +23,7 @@ network trained on 2048 solver-generated pairs from 8 configurations at
 under `workload_summary`.
 
   python bench.py [--steps K] [--warmup W] [--gpus N] [--impl reference]
-                  [--no-extra] [--no-mg] [--no-ptc] [--ptc-quick]
+                  [--no-extra] [--no-mg] [--no-ptc] [--ptc-quick] [--variant direct|staged]
 """
 from __future__ import annotations
 
@@ -440,10 +441,15 @@ def run_ours(args, rank, world, local_rank):
                              "status": tm.STATUS_NAMES[info.status]}
             if "fp64_cg" in tts and tts["chosen"]["seconds"] > 0:
                 tts["speedup_vs_fp64_cg"] = round(tts["fp64_cg"]["seconds"] / tts["chosen"]["seconds"], 3)
+        dw_rec = None
+        if rank == 0 and not args.no_extra:
+            dw_rec = run_reliable_update_operator(tm, ctx, bd, dev)
     finally:
         tm.tm_destroy(ctx)
 
     extra = {}
+    if dw_rec is not None:
+        extra["reliable_update_operator_32x64"] = dw_rec
     if rank == 0 and not args.no_extra:
         extra["multishift_heavy_24x48"] = run_multishift(tm, args)
         extra["batch_uneven_24"] = run_batch(tm, args)
@@ -499,6 +505,9 @@ def run_ours(args, rank, world, local_rank):
 def summarize(extra):
     """Seconds to solution of each extra workload, a few numbers per workload."""
     out = {}
+    ru = extra.get("reliable_update_operator_32x64", {})
+    if "double_word_ms" in ru:
+        out["reliable_update_op_32x64_ms"] = {"fp64": ru["fp64_ms"], "double_word": ru["double_word_ms"]}
     ms = extra.get("multishift_heavy_24x48", {})
     if "single_refined" in ms:
         out["multishift_24x48_s"] = {k: ms[k]["seconds"] for k in
@@ -534,6 +543,38 @@ def summarize(extra):
 def _sync():
     import torch
     torch.cuda.synchronize()
+
+
+def run_reliable_update_operator(tm, ctx, bd, dev, reps=10):
+    """The operator of the mixed solvers' reliable updates, M_hat^dag M_hat on
+    native FP64 fields at the workload's lattice: native FP64 arithmetic
+    (tm_apply_Mhat) against double-word arithmetic (tm_apply_Mhat_dw, its
+    conversions included), CUDA events, and the relative L2 difference of the
+    two results."""
+    import torch
+    nbytes = tm.tm_field_bytes(ctx, tm.TM_F64, 1)
+    a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    o64 = torch.empty_like(a)
+    odw = torch.empty_like(a)
+    tm.tm_field_import(ctx, tm.TM_F64, 1, a, bd)
+    out = {"op": "M_hat^dag M_hat on native FP64 fields"}
+    for name, f in (("fp64_ms", lambda: tm.tm_apply_Mhat(ctx, tm.TM_MDAGM, tm.TM_F64, o64, a)),
+                    ("double_word_ms", lambda: tm.tm_apply_Mhat_dw(ctx, tm.TM_MDAGM, odw, a))):
+        f()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            f()
+        e1.record()
+        torch.cuda.synchronize()
+        out[name] = round(e0.elapsed_time(e1) / reps, 4)
+    x = o64.view(torch.float64)
+    y = odw.view(torch.float64)
+    out["rel_l2_difference"] = float(torch.linalg.vector_norm(x - y) / torch.linalg.vector_norm(x))
+    out["speedup"] = round(out["fp64_ms"] / out["double_word_ms"], 3)
+    return out
 
 
 def run_multishift(tm, args):

@@ -79,8 +79,11 @@ def test_workload_summary_keeps_the_times():
     extra = {"batch_uneven_24": {"batched_s": 0.48, "sequential_s": 0.59},
              "mg_gcr_48x96": {"mg_setup_s": 5.9, "mg_gcr_s": 28.9, "mg_gcr_iters": 381, "eo_mixed_cg_s": 1.08,
                               "speedup_mg_vs_eo_mixed_cg": 0.037, "mg_gcr": {"iters": 381}},
-             "ptc_fcg_48x96": {"error": "RuntimeError('x')"}}
+             "ptc_fcg_48x96": {"error": "RuntimeError('x')"},
+             "reliable_update_operator_32x64": {"fp64_ms": 9.8, "double_word_ms": 3.7, "speedup": 2.65,
+                                                "rel_l2_difference": 6e-15}}
     out = bench.summarize(extra)
+    assert out["reliable_update_op_32x64_ms"] == {"fp64": 9.8, "double_word": 3.7}
     assert out["batch_24_s"] == {"batched": 0.48, "sequential": 0.59}
     assert out["mg_48x96"]["mg_gcr_iters"] == 381 and "mg_gcr" not in out["mg_48x96"]
     assert out["ptc_48x96"]["error"].startswith("RuntimeError")
