@@ -180,7 +180,9 @@ tm_status tm_field_norm2_noalloc(const tm_ctx* ctx, tm_prec prec, int nflavour, 
 
 /* out = op(in), native fields of precision prec on the device (eq:hQpm / eq:hQh).
  * Light ops take nflavour-1 fields, heavy ops nflavour-2 fields.  out != in.
- * Returns TM_ERR_STALE if the clover term predates the gauge field.  Operator
+ * Returns TM_ERR_STALE if the clover term predates the gauge field, TM_ERR_ARG
+ * for a field that is not device memory (checked before any launch, as in
+ * every call that takes a native field).  Operator
  * calls on one context share its intermediate fields: issue them on one stream
  * (field imports and exports may run on others). */
 tm_status tm_apply_Mhat(tm_ctx* ctx, tm_op op, tm_prec prec, void* out, const void* in,

@@ -77,6 +77,12 @@ static bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// native fields live in device memory: a host pointer handed to a kernel would
+// fault the GPU, so the entry points reject it first
+static bool device_fields(const void* a, const void* b = nullptr) {
+    return is_device_ptr(a) && (b == nullptr || is_device_ptr(b));
+}
+
 // pinned (page-locked or registered) host memory: copies from / to it stay
 // asynchronous, so the field calls need not synchronise
 static bool is_pinned_host(const void* p) {
@@ -486,6 +492,7 @@ extern "C" tm_status tm_apply_Mhat(tm_ctx* c, tm_op op, tm_prec prec, void* out,
     if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_Mhat: fields must be 16-byte aligned");
     if (op < TM_QHAT_PLUS || op > TM_WHAT_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat: unknown op %d", (int)op);
     CKS(check_prec(prec));
+    if (!device_fields(out, in)) return fail(TM_ERR_ARG, "tm_apply_Mhat: fields must be device pointers");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     CKS(ensure_prec(c, prec, st));
@@ -519,6 +526,7 @@ extern "C" tm_status tm_apply_Mhat_dw(tm_ctx* c, tm_op op, void* out, const void
     if (!c || !out || !in || out == in) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: bad pointers");
     if (((uintptr_t)out | (uintptr_t)in) & 15) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: fields must be 16-byte aligned");
     if (op < TM_QHAT_PLUS || op > TM_WHAT_SQ) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: unknown op %d", (int)op);
+    if (!device_fields(out, in)) return fail(TM_ERR_ARG, "tm_apply_Mhat_dw: fields must be device pointers");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     CKS(ensure_prec(c, P64, st));
@@ -545,6 +553,7 @@ extern "C" tm_status tm_apply_even(tm_ctx* c, tm_op op, tm_prec prec, void* out,
     if (op != TM_QHAT_PLUS && op != TM_QHAT_MINUS && op != TM_QH && op != TM_QH_DAG)
         return fail(TM_ERR_ARG, "tm_apply_even: op must be a single Schur operator");
     CKS(check_prec(prec));
+    if (!device_fields(out, in)) return fail(TM_ERR_ARG, "tm_apply_even: fields must be device pointers");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     CKS(ensure_prec(c, prec, st));
@@ -602,6 +611,7 @@ extern "C" tm_status tm_field_import(tm_ctx* c, tm_prec prec, int nf, void* dst,
     if (!c || !dst || !src || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_import: bad argument");
     if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_import: pointers must be 16-byte aligned");
     CKS(check_prec(prec));
+    if (!device_fields(dst)) return fail(TM_ERR_ARG, "tm_field_import: the native field must be a device pointer");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     if (is_device_ptr(src)) {
@@ -623,6 +633,7 @@ extern "C" tm_status tm_field_export(tm_ctx* c, tm_prec prec, int nf, double* ds
     if (!c || !dst || !src || (nf != 1 && nf != 2)) return fail(TM_ERR_ARG, "tm_field_export: bad argument");
     if (((uintptr_t)dst | (uintptr_t)src) & 15) return fail(TM_ERR_ARG, "tm_field_export: pointers must be 16-byte aligned");
     CKS(check_prec(prec));
+    if (!device_fields(src)) return fail(TM_ERR_ARG, "tm_field_export: the native field must be a device pointer");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     if (is_device_ptr(dst)) {
@@ -700,6 +711,7 @@ extern "C" tm_status tm_kernel_times(tm_ctx* c, tm_op op, tm_prec prec, const vo
     if (op != TM_QHAT_PLUS && op != TM_QHAT_MINUS && op != TM_QH && op != TM_QH_DAG)
         return fail(TM_ERR_ARG, "tm_kernel_times: op must be a single Schur operator");
     CKS(check_prec(prec));
+    if (!device_fields(in)) return fail(TM_ERR_ARG, "tm_kernel_times: in must be a device pointer");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     CKS(ensure_prec(c, prec, st));
@@ -877,7 +889,7 @@ extern "C" tm_status tm_field_norm2(tm_ctx* c, tm_prec prec, int nf, const void*
     if (((uintptr_t)field & 15) || ((uintptr_t)result & 7))
         return fail(TM_ERR_ARG, "tm_field_norm2: misaligned pointer");
     CKS(check_prec(prec));
-    if (!is_device_ptr(result)) return fail(TM_ERR_ARG, "tm_field_norm2: result must be a device pointer");
+    if (!device_fields(field, result)) return fail(TM_ERR_ARG, "tm_field_norm2: field and result must be device pointers");
     CK(cudaSetDevice(c->device));
     const cudaStream_t st = S(stream);
     switch (prec) {

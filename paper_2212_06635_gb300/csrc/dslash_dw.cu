@@ -52,7 +52,6 @@ __device__ __forceinline__ void cs_fma(CSum& a, df x, df y, float sg = 1.f) {
 __device__ __forceinline__ df cs_get(CSum a) { return df_fast_two_sum(a.h, a.l); }
 __device__ __forceinline__ CSum cs_zero() { return CSum{0.f, 0.f}; }
 
-__device__ __forceinline__ df dneg(df x, bool n) { return n ? df(-x.h, -x.l) : x; }
 __device__ __forceinline__ df dscale(df x, float s) { return df(s * x.h, s * x.l); }   // s = +-1
 // i^k z for k = 0 (z) or 1 (i z), times sg = +-1
 __device__ __forceinline__ cpx<df> cmul_unit(cpx<df> z, bool imag, float sg) {

@@ -97,6 +97,39 @@ def test_double_word_copies_follow_the_gauge_field():
         lat.close()
 
 
+def test_host_pointers_for_native_fields_are_rejected():
+    """Native fields must be device memory: every entry point that hands one to a
+    kernel returns TM_ERR_ARG for a host pointer before launching anything."""
+    import torch
+    dims = (4, 4, 4, 4)
+    lat = Lat(F.gauge_field(dims, 41), dims, KAPPA, CSW, mu=MU)
+    tm = lat.tm
+    try:
+        nb = tm.tm_field_bytes(lat.ctx, 0, 1)
+        dev = lat.native(0, 1)
+        host = np.zeros(nb // 8 + 2, dtype=np.float64)   # 16-byte aligned numpy buffer
+        hp = host.ctypes.data
+        hp += (-hp) % 16
+        dp = dev.data_ptr()
+        canon = torch.zeros(lat.vh * 24, dtype=torch.float64, device="cuda:0")
+        res = torch.zeros(1, dtype=torch.float64, device="cuda:0")
+        calls = [
+            ("tm_apply_Mhat", lambda: tm.lib.tm_apply_Mhat(lat.ctx, tm.TM_MDAGM, 0, hp, dp, None)),
+            ("tm_apply_Mhat", lambda: tm.lib.tm_apply_Mhat(lat.ctx, tm.TM_MDAGM, 0, dp, hp, None)),
+            ("tm_apply_Mhat_dw", lambda: tm.lib.tm_apply_Mhat_dw(lat.ctx, tm.TM_MDAGM, hp, dp, None)),
+            ("tm_apply_even", lambda: tm.lib.tm_apply_even(lat.ctx, tm.TM_QHAT_PLUS, 0, hp, dp, None)),
+            ("tm_field_import", lambda: tm.lib.tm_field_import(lat.ctx, 0, 1, hp, canon.data_ptr(), None)),
+            ("tm_field_export", lambda: tm.lib.tm_field_export(lat.ctx, 0, 1, canon.data_ptr(), hp, None)),
+            ("tm_field_norm2", lambda: tm.lib.tm_field_norm2(lat.ctx, 0, 1, hp, res.data_ptr(), None)),
+        ]
+        for name, call in calls:
+            assert call() == tm.TM_ERR_ARG, name
+            assert "device pointer" in tm.tm_last_error(), name
+        torch.cuda.synchronize()   # nothing was launched with the host address
+    finally:
+        lat.close()
+
+
 def test_periodic_time_boundary():
     dims = (4, 4, 2, 6)
     u = F.gauge_field(dims, 31)
