@@ -138,6 +138,7 @@ def test_periodic_time_boundary():
     try:
         psi = F.odd_spinor(dims, 32)
         assert rel(lat.apply(lat.tm.TM_QHAT_PLUS, 0, psi), op.Qhat(psi, +1)) < 1e-13
+        assert rel(lat.apply_dw(lat.tm.TM_MDAGM, psi), op.MdagM(psi)) < 2 * DW_TOL
     finally:
         lat.close()
 
