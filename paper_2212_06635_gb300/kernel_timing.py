@@ -9,7 +9,10 @@ here, and the ncu captures under profiles/ run these same launch sequences.
   ... --ptc                       a 1-8-8-8-1 PTC network applied 1 + reps times
   ... --ptc-grad                  loss and gradient of that network, 1 + reps times
   ... --ptc-fcg ITERS             ITERS iterations of PTC-preconditioned flexible CG
-  ... --solve                     one mixed-precision CG solve (--prec storage) to 1e-10
+  ... --solve [--solves N] [--delta D]
+                                  N mixed-precision CG solves (--prec storage) to 1e-10
+  ... --dw [--heavy]              the normal operator on FP64 fields, native FP64 and
+                                  double-word (the reliable updates' operator), 1 + reps each
   ... --multishift                a 12-shift heavy-doublet multishift solve (--prec storage)
   ... --mg ITERS                  multigrid setup and ITERS multigrid-preconditioned GCR iterations
   ... --fma                       measured FP64 and FP32 FMA rates of the CUDA cores
