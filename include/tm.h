@@ -101,6 +101,10 @@ typedef struct {
                             sloppy.  TM_F16 after an FP32 multishift is Sec. 4.2's
                             "single precision MS-CG with double-half shift-by-shift
                             refinement" */
+    int fp64_updates;    /* mixed solvers: 1 recomputes every reliable-update residual
+                            with the native FP64 operator; 0 (default) uses the
+                            double-word operator (tm_apply_Mhat_dw) and FP64 only to
+                            confirm a residual below tol */
 } tm_solve_params;
 
 typedef struct {

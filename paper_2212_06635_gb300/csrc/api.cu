@@ -1030,10 +1030,11 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
     double rr = 0;
     bool x0 = false;
     CKS(is_zero64<NF>(c, x64, st, &x0));
-    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, x0, PS != P64));
+    const bool dw = PS != P64 && !sp->fp64_updates;   // double-word reliable updates
+    CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, x0, dw));
     const double target = tol * tol * bb;
     // an initial guess already within the tolerance is confirmed in FP64
-    if (PS != P64 && !x0 && rr <= target)
+    if (dw && !x0 && rr <= target)
         CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
     tm_status status = TM_OK;
     cudaGraphExec_t gexec = nullptr;
@@ -1080,11 +1081,11 @@ static tm_status solve_core(tm_ctx* c, tm_op op, double shift, const tm_solve_pa
                 CK((launch_add_to64<P32, NC, 1>(vb1(c, x64, xs), nb, st)));
                 CK(cudaMemsetAsync(xs, 0, spinor_bytes(P32, NC, vh), st));
             }
-            CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, false, PS != P64));
+            CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr, false, dw));
             info->reliable_updates += 1;
             // a double-word residual below the target is confirmed in FP64 (the
             // returned true residual is always an FP64 one)
-            if (PS != P64 && rr <= target)
+            if (dw && rr <= target)
                 CKS(true_residual<NF>(c, op, shift, x64, b64, r64, ax64, mid64, te64, st, &rr));
             if (rr <= target) break;
             if (h.flag == CTL_MAXITER || h.iter >= maxiter || !std::isfinite(rr)) {
@@ -1799,9 +1800,9 @@ static tm_status batch_core(tm_ctx** cs, int n, tm_op op, const tm_solve_params*
             const int saved_flag = h.flag;
             const double rr_old = h.rr_old;
             const int iters = h.iter;
-            CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q], false,
-                                 PS != P64));
-            if (PS != P64 && rr[q] <= tol * tol * bb[q])   // confirmed in FP64
+            const bool dw = PS != P64 && !sp->fp64_updates;
+            CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q], false, dw));
+            if (dw && rr[q] <= tol * tol * bb[q])   // confirmed in FP64
                 CKS(true_residual<1>(c, op, 0.0, w[q].x64, w[q].b64, r64, ax64, mid64, te64, st, &rr[q]));
             infos[q].reliable_updates += 1;
             // true_residual overwrote h.shift only; restore the control word
@@ -2438,8 +2439,9 @@ extern "C" tm_status tm_solve_fcg(tm_ctx* c, tm_op op, tm_ptc* n, const tm_solve
         }
         if (status != TM_OK) break;
         CK((launch_add_to64<P32, 12, 1>(vb1(c, x64, xs), nb, st)));
-        CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr, false, true));
-        if (rr <= target)   // confirmed in FP64
+        const bool dw = !sp->fp64_updates;
+        CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr, false, dw));
+        if (dw && rr <= target)   // confirmed in FP64
             CKS(true_residual<1>(c, op, 0.0, x64, b64, r64, ax64, mid64, te64, st, &rr));
         info->reliable_updates += 1;
         if (its >= maxiter && rr > target) { status = TM_ERR_NOT_CONVERGED; break; }

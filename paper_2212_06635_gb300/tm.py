@@ -35,7 +35,8 @@ class tm_params(ct.Structure):
 
 class tm_solve_params(ct.Structure):
     _fields_ = [("tol", ct.c_double), ("maxiter", ct.c_int), ("sloppy", ct.c_int),
-                ("delta", ct.c_double), ("chunk", ct.c_int), ("use_graph", ct.c_int), ("refine", ct.c_int)]
+                ("delta", ct.c_double), ("chunk", ct.c_int), ("use_graph", ct.c_int), ("refine", ct.c_int),
+                ("fp64_updates", ct.c_int)]
 
 
 class tm_solve_info(ct.Structure):
@@ -247,10 +248,12 @@ def tm_apply_even(ctx, op, prec, out, inp, stream=None):
     _check(lib.tm_apply_even(ctx, int(op), int(prec), ptr(out), ptr(inp), _stream(stream)))
 
 
-def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.0, chunk=16, use_graph=1, refine=TM_F64):
+def solve_params(tol=1e-10, maxiter=100000, sloppy=TM_F64, delta=0.0, chunk=16, use_graph=1, refine=TM_F64,
+                 fp64_updates=0):
     """refine: multishift refinement storage precision (TM_F64 = same as sloppy);
-    delta <= 0: the library's reliable-update threshold for the sloppy precision."""
-    return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph, refine)
+    delta <= 0: the library's reliable-update threshold for the sloppy precision;
+    fp64_updates: reliable-update residuals with the native FP64 operator."""
+    return tm_solve_params(tol, maxiter, sloppy, delta, chunk, use_graph, refine, int(fp64_updates))
 
 
 def tm_solve_cg(ctx, op, sp, x, b, stream=None, check=True):

@@ -57,6 +57,26 @@ def test_mixed_precision_cg_8x8(sloppy, graph):
         lat.close()
 
 
+def test_fp64_reliable_updates_option():
+    """tm_solve_params.fp64_updates = 1 recomputes every reliable-update residual
+    with the native FP64 operator: the same solve converges to the same
+    tolerance, with the same iteration count to within a few."""
+    dims = (8, 8, 8, 8)
+    op, lat = _lat(dims, 1100, kappa=0.1400, mu=0.005)
+    tm = lat.tm
+    try:
+        b = F.odd_spinor(dims, 2100)
+        infos = []
+        for upd in (0, 1):
+            x = to_dev(np.zeros_like(b))
+            sp = tm.solve_params(tol=1e-10, sloppy=tm.TM_F16, fp64_updates=upd)
+            infos.append(tm.tm_solve_cg(lat.ctx, tm.TM_MDAGM, sp, x, to_dev(b)))
+            assert S.rel_residual(op.MdagM, from_dev(x, b.shape), b) <= 1.05e-10
+        assert abs(infos[0].iters - infos[1].iters) <= 3
+    finally:
+        lat.close()
+
+
 def test_qpqm_and_host_pointers_and_initial_guess():
     dims = (6, 4, 4, 6)
     op, lat = _lat(dims, 1200)
