@@ -60,3 +60,41 @@ def test_binding_structs_match_the_c_layout(tmp_path):
         assert ct.sizeof(cls) == c_layout[(name, "size")], name
         for mem in members:
             assert getattr(cls, mem).offset == c_layout[(name, mem)], (name, mem)
+
+
+def _prototypes():
+    text = re.sub(r"/\*.*?\*/", "", HDR.read_text(), flags=re.S)
+    out = {}
+    for ret, name, args in re.findall(r"(tm_status|const char\s*\*)\s+(tm_\w+)\s*\(([^)]*)\)\s*;", text):
+        out[name] = [a.strip() for a in args.split(",")] if args.strip() not in ("", "void") else []
+    return out
+
+
+def _c_kind(decl):
+    if "*" in decl or "[" in decl:
+        return "p"
+    t = decl.rsplit(None, 1)[0] if len(decl.split()) > 1 else decl
+    if "double" in t:
+        return "d"
+    if "long long" in t:
+        return "q"
+    return "i"   # int and the tm_* enums
+
+
+def _ct_kind(t):
+    if t in (ct.c_void_p, ct.c_char_p) or hasattr(t, "_type_") and isinstance(t, type) and issubclass(t, ct._Pointer):
+        return "p"
+    return {ct.c_double: "d", ct.c_int: "i", ct.c_ulonglong: "q"}[t]
+
+
+def test_binding_signatures_match_the_header():
+    """Every bound entry point takes the header's number and kinds of arguments
+    (pointer, int or enum, double, 64-bit integer), in order."""
+    from paper_2212_06635_gb300 import tm
+    protos = _prototypes()
+    assert len(protos) >= 50
+    for name, argtypes in tm._sigs.items():
+        assert name in protos, name
+        c_kinds = [_c_kind(a) for a in protos[name]]
+        py_kinds = [_ct_kind(t) for t in argtypes]
+        assert c_kinds == py_kinds, (name, c_kinds, py_kinds)
